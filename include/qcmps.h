@@ -1,0 +1,215 @@
+/*
+ * qcmps — noisy-shot sampling of cultivation-shaped Clifford+T circuits on a B300 (sm_103a).
+ *
+ * C ABI of the library.  Every step of the sampling path runs in the library's own CUDA kernels;
+ * the caller provides device memory and a CUDA stream.  All functions are thread-safe unless
+ * stated otherwise.  Every function returns a qc_status; on failure qc_last_error() returns a
+ * thread-local message and the outputs are unspecified.
+ *
+ * The problem statement follows Sec. 4 of "Comparing magic state cultivation methods using
+ * matrix product states" (arXiv 2609.19116): a circuit of Clifford gates and T gates on a line
+ * of qubits with Z measurements and resets; uniform depolarising noise of rate p (each of the
+ * 4^k-1 non-identity Paulis of a k-qubit channel with probability p/(4^k-1)); a shot is kept only
+ * if every measurement returns 0, and a kept shot is logically wrong when its final state's
+ * squared overlap with the noiseless final state differs from 1 (Sec. 4, App. A.3).  Counts are
+ * kept per fault weight w, the number of channels that fired (Sec. 4.1, Eq. estimators).
+ *
+ * Circuit text format: one instruction per line, '#' comments:
+ *   QUBITS n | H q | S q | SDG q | X q | Y q | Z q | T q | TDG q | CX c t | CZ a b | SWAP a b |
+ *   M q (Z measurement, post-selected on 0) | R q (reset to |0>) |
+ *   DEP1 q | DEP2 a b (depolarising channels) | XERR q (X error channel) | TICK (no-op)
+ * Noise channels are numbered 0.. in text order; readouts (M and R) likewise.
+ *
+ * Random numbers (Philox4x32-10, Salmon et al. SC'11; key = (seed mod 2^32, seed >> 32)):
+ *   T1 = floor(p 2^32); y = 1 - T1/2^32; TG[s] = floor((1 - y^(s+1)) 2^32) for s = 0..63, the
+ *   powers formed by successive FP64 multiplications.  Shots form 64-shot words w = shot >> 6.
+ *   - channel c, word w: u = philox(c>>2, w, 0, 0)[c&3]; first faulted lane = min{s: u < TG[s]}
+ *     (none if u >= TG[63]); further lanes by geometric skips from d_k = philox(c, w, k>>2, 1)[k&3],
+ *     next lane = previous + 1 + min{s: d_k < TG[s]} while < 64.
+ *   - Pauli of faulted lane j: x = philox(c, w, j, 2)[0]; code = 1 + (x*z >> 32), z = 3 (DEP1) or 15
+ *     (DEP2, code i = (P_a, P_b) = (i>>2, i&3), 0=I 1=X 2=Y 3=Z); XERR is always X.
+ *   - readout k of shot s: x = philox(k, s mod 2^32, s >> 32, 3); u = ((x0>>5) 2^26 + (x1>>6)) / 2^53;
+ *     outcome 1 iff u < p1 (FP64).
+ *   - fixed weight w (subset sampling, Sec. 4.1): Floyd's algorithm over the channels with draws
+ *     philox(i, s mod 2^32, s >> 32, 4)[0] reduced to [0, j] by Lemire's multiply-shift with
+ *     rejection; the Pauli of a chosen channel c from philox(c, s mod 2^32, s >> 32, 5)[0].
+ */
+#ifndef QCMPS_H
+#define QCMPS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    QC_OK = 0,
+    QC_PENDING = 1,      /* job not finished yet (mps_serve_poll) */
+    QC_EINVAL = -1,      /* invalid argument or malformed circuit text */
+    QC_ENOMEM = -2,      /* device or host allocation failed, or admission impossible */
+    QC_EDEVICE = -3,     /* CUDA error */
+    QC_ENOCONV = -4,     /* an SVD did not converge within its sweep limit */
+    QC_ETIMEOUT = -5,    /* a bounded wait ran out */
+    QC_ECANCELLED = -6,  /* job cancelled */
+    QC_ECAPACITY = -7    /* a fixed-size buffer was too small (see the call's documentation) */
+} qc_status;
+
+/* Thread-local message describing the last failure of a call made on this thread. */
+const char* qc_last_error(void);
+
+/* ---- circuits --------------------------------------------------------------------------- */
+
+typedef struct qc_circuit qc_circuit; /* opaque, owned by the library */
+
+typedef struct {
+    int32_t n_qubits;
+    int64_t n_ops;           /* instructions other than QUBITS/TICK */
+    int64_t n_channels;      /* noise channels M (Sec. 4.1) */
+    int64_t n_measurements;  /* M instructions */
+    int64_t n_decided;       /* measurements decided by stabiliser tracking (Sec. 4.2) */
+    int64_t n_resets;
+    int64_t n_t;             /* T and T^dagger gates */
+    int64_t n_mps_updates;   /* two-site updates per shot after SWAP routing and centre moves */
+} qc_circuit_info;
+
+/* Parse circuit text (len bytes, need not be NUL-terminated).  Runs the offline analysis of
+ * Sec. 4.2 (stabiliser tracking through diagonal non-Clifford gates; a measurement is decided
+ * when +-Z_q is in the tracked group) and compiles the device programs.  *out is owned by the
+ * library; release it with qc_circuit_free.  QC_EINVAL on malformed text. */
+qc_status qc_circuit_parse(const char* text, size_t len, qc_circuit** out);
+void qc_circuit_free(qc_circuit* circuit);
+qc_status qc_circuit_get_info(const qc_circuit* circuit, qc_circuit_info* out);
+/* flags[i] = 1 when the i-th M instruction (text order) is decided (Sec. 4.2).  Host buffer of
+ * n_measurements bytes. */
+qc_status qc_circuit_decided(const qc_circuit* circuit, uint8_t* flags);
+
+/* ---- noise ---------------------------------------------------------------------------- */
+
+typedef struct {
+    double p;              /* uniform channel rate, 0 <= p < 1 (Sec. 4) */
+    uint64_t seed;         /* Philox key */
+    int32_t fault_weight;  /* -1: independent channels (Bernoulli p); w >= 0: exactly w faults */
+} qc_noise;
+
+/* Fault configurations of the given shots (Sec. 4: each channel resolves to a Pauli).
+ * shots_dev: device array of nshots shot indices.  Outputs (device, caller-owned):
+ * count_dev[i] = number of faults of shot i; chan_dev[i*max_faults + k], code_dev[...] its
+ * faults sorted by channel (pauli code as in the header comment).  Shots with more than
+ * max_faults faults have count_dev[i] = that number and only max_faults entries written.
+ * Asynchronous on `stream` (a cudaStream_t, NULL = legacy default stream). */
+qc_status qc_sample_faults(const qc_circuit* circuit, qc_noise noise, const uint64_t* shots_dev,
+                           uint64_t nshots, uint32_t max_faults, uint32_t* count_dev,
+                           uint32_t* chan_dev, uint8_t* code_dev, void* stream);
+
+/* ---- pre-screen (Sec. 4.2) ----------------------------------------------------------- */
+
+typedef struct {
+    uint64_t* shots_dev;   /* caller-owned device buffer of `capacity` shot indices */
+    uint64_t capacity;
+    uint64_t count;        /* out: number of surviving shots (may exceed capacity; then only
+                              the first `capacity`, in increasing order, are written) */
+} qc_survivors;
+
+/* Pauli-frame pre-screen of shots [shot0, shot0 + nshots) (shot0 a multiple of 64): per shot, the
+ * fault configuration is propagated as a Pauli frame through the Clifford part (diagonal
+ * non-Clifford gates leave it unchanged) and the shot is discarded when a decided measurement
+ * flips; it never discards a shot that post-selection would keep (Sec. 4.2).
+ *   kept_mask_dev  device, ceil(nshots/64) words; bit i of word k <-> shot shot0 + 64k + i
+ *   survivors      optional (NULL): surviving shot indices, increasing
+ *   hist_drawn, hist_kept  optional host arrays of w_max+1 counts: shots per fault weight w
+ *                  (bin w_max collects w >= w_max), all drawn / surviving
+ * Bernoulli noise only (fault_weight = -1).  Synchronises `stream` before returning. */
+qc_status pauli_prescreen(const qc_circuit* circuit, qc_noise noise, uint64_t shot0,
+                          uint64_t nshots, uint64_t* kept_mask_dev, qc_survivors* survivors,
+                          uint64_t* hist_drawn, uint64_t* hist_kept, int32_t w_max, void* stream);
+
+/* ---- batched MPS sampling (Sec. 3.1, 4, 4.3) --------------------------------------------- */
+
+enum { QC_C64 = 0, QC_C128 = 1 };
+
+typedef struct {
+    int32_t chi_max;     /* bond dimension cap */
+    double cutoff;       /* discarded-weight cutoff of the truncation rule */
+    int32_t precision;   /* QC_C64: complex64 site tensors and SVD, FP64 probabilities and
+                            discarded weight; QC_C128: complex128 throughout */
+    double tau;          /* logical-error threshold on 1 - F; <= 0 selects 1e-8 (C128) or
+                            max(1e-3, 10 * discarded weight) (C64) */
+} qc_mps_params;
+
+typedef struct { uint64_t n, n_acc, n_err; } qc_counts;
+
+typedef struct {
+    uint64_t shot;
+    int32_t status;          /* 0 accepted, 1 rejected by a measurement, <0 a qc_status */
+    int32_t weight;          /* fault weight w */
+    int32_t logical_error;   /* accepted and 1 - F > tau */
+    int32_t chi_peak;        /* largest bond kept during the shot */
+    int64_t abort_op;        /* index (text order, instructions only) of the rejecting M, or -1 */
+    double fidelity;         /* F = |<psi_ref|psi>|^2 / (<psi_ref|psi_ref><psi|psi>) */
+    double discarded;        /* summed discarded weight of all truncations (FP64) */
+    int32_t degenerate_cuts; /* truncations whose last kept and first dropped values tie */
+    int32_t n_updates;       /* two-site updates performed */
+} qc_shot_result;
+
+/* Simulate the given shots (typically pre-screen survivors) as MPS: single-site gates in place;
+ * a two-site gate contracts the pair, applies the 4x4 gate and splits by SVD, keeping the
+ * smallest count of singular values whose discarded tail sum s_i^2 is <= cutoff * sum s_i^2,
+ * at most chi_max, renormalised (Sec. 3.1; the truncation rule itself is not fixed by the
+ * paper, which runs untruncated); SWAP routing for non-adjacent pairs (Sec. 3.1); a measurement
+ * samples the orthogonality-centre marginal in FP64, projects, renormalises and ends the shot
+ * when it returns 1 (Sec. 4.3).  At the end F is formed against the noiseless reference state.
+ *   shots_dev      device array of nshots shot indices
+ *   per_w          host array of w_max+1 counts, ACCUMULATED into (bin w_max collects w >= w_max):
+ *                  n = simulated shots, n_acc = accepted, n_err = accepted with a logical error
+ *   per_shot_dev   optional device array of nshots results
+ * Synchronises `stream` before returning.  QC_EINVAL if the noiseless circuit has a measurement
+ * that is not deterministically 0.  Per-shot failures are reported in per_shot_dev status. */
+qc_status mps_sample_batch(const qc_circuit* circuit, qc_noise noise, const uint64_t* shots_dev,
+                           uint64_t nshots, qc_mps_params params, qc_counts* per_w,
+                           int32_t w_max, qc_shot_result* per_shot_dev, void* stream);
+
+/* Bytes of device memory one in-flight shot needs (site tensors at their capacities plus the
+ * per-shot split scratch), the footprint used for admission. */
+qc_status mps_shot_footprint(const qc_circuit* circuit, qc_mps_params params, uint64_t* bytes);
+
+/* ---- serving loop ---------------------------------------------------------------------- */
+
+typedef struct qc_server qc_server;
+
+typedef struct {
+    uint64_t hbm_budget_bytes;  /* admission budget for in-flight MPS state */
+    int32_t max_slots;          /* upper bound on concurrently simulated shots (0 = default) */
+    int32_t n_streams;          /* device streams the loop spreads jobs over (0 = default 2) */
+} qc_serve_cfg;
+
+typedef struct {
+    int32_t state;              /* QC_OK done, QC_PENDING running/queued, or an error status */
+    uint64_t shots;             /* shots drawn */
+    uint64_t survivors;         /* shots kept by the pre-screen */
+    qc_counts counts[16];       /* per fault weight, bin 15 collects w >= 15 */
+    double submit_ms, start_ms, end_ms; /* on the server's clock */
+} qc_job_result;
+
+/* Start a request loop on the current device.  Jobs are admitted while their in-flight
+ * footprint fits the budget, are pre-screened, and their surviving shots are simulated in
+ * batches that mix the shots of all admitted jobs; a finished batch slot is back-filled from
+ * the queue.  *out is owned by the library; release with mps_serve_destroy. */
+qc_status mps_serve_create(const qc_serve_cfg* cfg, qc_server** out);
+/* Queue nshots shots [shot0, shot0 + nshots) of a circuit (shot0 a multiple of 64).  The circuit
+ * must stay alive until the job is done or cancelled. */
+qc_status mps_serve_submit(qc_server* server, const qc_circuit* circuit, qc_noise noise,
+                           qc_mps_params params, uint64_t shot0, uint64_t nshots,
+                           uint64_t* job_id);
+/* QC_PENDING while the job runs; QC_OK with *out filled when done. */
+qc_status mps_serve_poll(qc_server* server, uint64_t job_id, qc_job_result* out);
+qc_status mps_serve_cancel(qc_server* server, uint64_t job_id);
+/* Stops the loop (cancelling queued jobs) and frees everything. */
+void mps_serve_destroy(qc_server* server);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QCMPS_H */

@@ -127,26 +127,69 @@ def word_events(seed: int, n_channels: int, words, tg):
     return u < tg[63]
 
 
+def first_below_vec(u, tg):
+    """Vectorised: smallest s with u < tg[s], or 64."""
+    return np.searchsorted(tg, u, side="right")
+
+
 def sample_faults_bernoulli(seed: int, channel_kinds, p: float, shots):
     """Per shot: sorted list of (channel, pauli code) under independent Bernoulli(p) channels.
 
     Follows Sec. 4: every channel independently resolves to a non-identity Pauli with probability
-    p (quantised to T1/2^32 by the contract), uniformly among the 4^k-1 strings."""
+    p (quantised to T1/2^32 by the contract), uniformly among the 4^k-1 strings.  The draws are
+    those of `faulted_lanes` and `pauli_code`, evaluated for all (channel, word) events at once."""
     shots = [int(s) for s in shots]
     _, tg = thresholds(p)
     words = sorted({s >> 6 for s in shots})
     out = {s: [] for s in shots}
     if not words or not channel_kinds:
         return out
-    ev = word_events(seed, len(channel_kinds), words, tg)
-    want = {}
+    k0, k1 = key_of(seed)
+    wanted = {}
     for s in shots:
-        want.setdefault(s >> 6, set()).add(s & 63)
-    for ci, wi in zip(*np.nonzero(ev)):
-        c, w = int(ci), words[int(wi)]
-        for lane in faulted_lanes(seed, c, w, tg):
-            if lane in want[w]:
-                out[(w << 6) | lane].append((c, pauli_code(seed, c, w, lane, channel_kinds[c])))
+        wanted.setdefault(s >> 6, set()).add(s & 63)
+    # word-level draws, in blocks of words to bound memory
+    ev_c, ev_w, ev_u = [], [], []
+    groups = np.arange((len(channel_kinds) + 3) // 4, dtype=np.uint64)
+    for b in range(0, len(words), 256):
+        wb = np.array(words[b:b + 256], dtype=np.uint64)
+        G, Wd = np.meshgrid(groups, wb, indexing="ij")
+        x = philox4x32_10(G, Wd, 0, TAG_WORD, k0, k1)
+        u = np.stack(x, axis=1).reshape(len(groups) * 4, len(wb))[:len(channel_kinds)]
+        ci, wi = np.nonzero(u < tg[63])
+        ev_c.append(ci.astype(np.uint64))
+        ev_w.append(wb[wi])
+        ev_u.append(u[ci, wi])
+    ev_c = np.concatenate(ev_c)
+    ev_w = np.concatenate(ev_w)
+    lane = first_below_vec(np.concatenate(ev_u), tg).astype(np.int64)
+    pairs = [(ev_c, ev_w, lane.copy())]
+    active = np.ones(len(lane), dtype=bool)
+    k = 0
+    while active.any():
+        idx = np.nonzero(active)[0]
+        d = philox4x32_10(ev_c[idx], ev_w[idx], k >> 2, TAG_SKIP, k0, k1)[k & 3]
+        s = first_below_vec(d, tg).astype(np.int64)
+        nl = lane[idx] + 1 + s
+        ok = (s < 64) & (nl < 64)
+        lane[idx[ok]] = nl[ok]
+        active[idx[~ok]] = False
+        pairs.append((ev_c[idx[ok]], ev_w[idx[ok]], nl[ok]))
+        k += 1
+    C = np.concatenate([pp[0] for pp in pairs])
+    Wv = np.concatenate([pp[1] for pp in pairs])
+    Lv = np.concatenate([pp[2] for pp in pairs])
+    keep = np.array([int(l) in wanted[int(w)] for w, l in zip(Wv, Lv)], dtype=bool)
+    C, Wv, Lv = C[keep], Wv[keep], Lv[keep]
+    xs = philox4x32_10(C, Wv, Lv.astype(np.uint64), TAG_PAULI, k0, k1)[0]
+    for c, w, l, x in zip(C.tolist(), Wv.tolist(), Lv.tolist(), xs.tolist()):
+        kind = channel_kinds[c]
+        if kind == "XERR":
+            code = 1
+        else:
+            z = 15 if kind == "DEP2" else 3
+            code = 1 + ((int(x) * z) >> 32)
+        out[(w << 6) | l].append((c, code))
     for s in out:
         out[s].sort()
     return out

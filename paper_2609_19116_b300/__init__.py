@@ -1,0 +1,8 @@
+"""qcmps: B300-native noisy-shot MPS sampling of cultivation-shaped Clifford+T circuits.
+
+The sampling path runs in the CUDA library libqcmps.so (include/qcmps.h); this package only
+binds it.  Importing it does not touch the GPU.
+"""
+from ._native import QC_C64, QC_C128, QcError  # noqa: F401
+from .api import (Circuit, Server, mps_sample_batch, pauli_prescreen, qc_sample_faults,  # noqa: F401
+                  SHOT_DTYPE)

@@ -1,0 +1,992 @@
+// Batched MPS shot engine (Sec. 3.1, Sec. 4, Sec. 4.3).
+//
+// Persistent launch: every CTA owns one shot slot (its site tensors in HBM plus a split scratch)
+// and pulls shot indices from a global counter until none is left, so a shot that post-selection
+// rejects early frees its slot at once for the next one (online screening, Sec. 4.3).  A shot walks
+// the compiled site-operation program: single-site gates in place; a two-site update contracts
+// the pair into theta (2chi_l x 2chi_r), applies the 4x4 gate and splits it by a one-sided
+// (Hestenes) Jacobi SVD held in shared memory whenever theta fits there; readouts take the
+// Born probability of the orthogonality-centre tensor in FP64.  At the end the normalised overlap
+// with the noiseless reference state decides the logical-error flag (Sec. 4, App. A.3).
+//
+// The split avoids accumulating V: Jacobi orthogonalises the columns of theta (centre moving
+// right) or of theta^H (centre moving left); the orthonormal factor is kept, and the centre
+// tensor is the projection of the saved theta on it.
+#include <cfloat>
+#include <cmath>
+#include <cstdio>
+#include <vector>
+
+#include "philox.cuh"
+#include "qc_internal.h"
+
+namespace qc {
+namespace {
+
+template <typename R> struct VecOf;
+template <> struct VecOf<float> { using T = float2; };
+template <> struct VecOf<double> { using T = double2; };
+
+template <typename V> __device__ __forceinline__ V cmk(decltype(V::x) a, decltype(V::x) b) { V v; v.x = a; v.y = b; return v; }
+template <typename V> __device__ __forceinline__ V cmul(V a, V b) { return cmk<V>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+template <typename V> __device__ __forceinline__ V cmulc(V a, V b) { return cmk<V>(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x); }  // conj(a)*b
+template <typename V> __device__ __forceinline__ V cadd(V a, V b) { return cmk<V>(a.x + b.x, a.y + b.y); }
+template <typename V> __device__ __forceinline__ V cfma(V a, V b, V c) {  // a*b + c
+    return cmk<V>(fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y)));
+}
+template <typename V> __device__ __forceinline__ V cfmac(V a, V b, V c) {  // conj(a)*b + c
+    return cmk<V>(fma(a.x, b.x, fma(a.y, b.y, c.x)), fma(a.x, b.y, fma(-a.y, b.x, c.y)));
+}
+
+constexpr int MAXF = 256;     // faults per shot
+constexpr int OPCH = 64;      // program ops staged per step
+
+template <typename R>
+struct EngineParams {
+    using V = typename VecOf<R>::T;
+    const MpsOp* prog;
+    uint32_t nops;
+    int nq;
+    const uint8_t* chan_kind;
+    uint32_t nchan;
+    const V* g1;  // [G1_COUNT][4]
+    const V* g4;  // [G4_COUNT][16]
+    const uint64_t* shots;
+    uint64_t ntasks;
+    unsigned long long* next_task;
+    V* mps;               // slot buffers
+    uint64_t slot_stride; // elements
+    const uint64_t* off;  // site offsets within a slot [nq+1]
+    const int* cap;       // bond capacities [nq+1]
+    V* scratch;           // per slot: X (global path) then theta copy
+    uint64_t scratch_stride;
+    uint64_t xg_elems;    // size of the X part of a slot's scratch
+    uint32_t x_smem;      // capacity (elements) of the shared-memory X
+    int chi_max;
+    double cutoff;
+    uint32_t k0, k1;
+    uint32_t tg[64];
+    int32_t weight;
+    int reference;        // 1: noiseless reference run writing into `mps` slot 0
+    const V* ref;         // reference state (same layout as one slot)
+    const int* ref_dims;  // [nq+1]
+    double ref_disc;
+    double ref_norm;
+    int final_center;
+    double tau;           // > 0 fixed threshold, else automatic
+    int precision;        // QC_C64 / QC_C128
+    qc_shot_result* per_shot;
+    unsigned long long* counts;  // [3*(wmax+1)]
+    int wmax;
+    int* ref_status;      // reference run: 0 ok, else index+1 of the bad measurement
+    int* ref_dims_out;    // reference run: bond dims [nq+1]
+    double* ref_disc_out;
+    int sweep_cap;
+};
+
+template <typename R>
+struct Shared {
+    using V = typename VecOf<R>::T;
+    V* X;         // [x_smem]
+    int* dims;    // [nq+1]
+    uint32_t* fch;
+    uint8_t* fcode;
+    R* sig2;      // [2*chi_cap]
+    int* perm;    // [2*chi_cap]
+    double* red;  // [64]
+    MpsOp* ops;   // [OPCH]
+};
+
+template <typename R>
+__device__ __forceinline__ R warp_sum(R v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    return v;
+}
+
+// Block-wide sum of a double; every thread gets the result.
+template <int NT>
+__device__ double block_sum(double v, double* red) {
+    v = warp_sum<double>(v);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    double t = 0;
+    if (threadIdx.x < 32) {
+        t = lane < NT / 32 ? red[lane] : 0.0;
+        t = warp_sum<double>(t);
+        if (lane == 0) red[32] = t;
+    }
+    __syncthreads();
+    return red[32];
+}
+
+template <typename R, int NT>
+struct Engine {
+    using V = typename VecOf<R>::T;
+    const EngineParams<R>& P;
+    Shared<R>& S;
+    V* slot;      // this CTA's site tensors
+    V* xg;        // global X
+    V* tcopy;     // theta copy
+    // per-shot state (uniform, kept in registers of every thread, updated identically)
+    int status;
+    double disc;
+    int degen;
+    int chi_peak;
+    int nupd;
+    int64_t abort_op;
+
+    __device__ Engine(const EngineParams<R>& p, Shared<R>& s, int slot_id)
+        : P(p), S(s) {
+        slot = P.mps + (uint64_t)slot_id * P.slot_stride;
+        xg = P.scratch + (uint64_t)slot_id * P.scratch_stride;
+        tcopy = xg + P.xg_elems;
+    }
+
+    __device__ V* site(int q) { return slot + P.off[q]; }
+
+    // ---- single-site gate in place: a[l,s,r] <- sum_t g[s,t] a[l,t,r] --------------------------
+    __device__ void apply1(int q, V g00, V g01, V g10, V g11) {
+        const int cl = S.dims[q], cr = S.dims[q + 1];
+        V* a = site(q);
+        for (int e = threadIdx.x; e < cl * cr; e += NT) {
+            const int l = e / cr, r = e - l * cr;
+            V* p0 = a + (l * 2) * cr + r;
+            V* p1 = p0 + cr;
+            const V x = *p0, y = *p1;
+            *p0 = cfma(g00, x, cmul(g01, y));
+            *p1 = cfma(g10, x, cmul(g11, y));
+        }
+        __syncthreads();
+    }
+
+    __device__ void apply_pauli(int q, uint32_t p) {
+        if (p == 0) return;
+        const V z = cmk<V>(0, 0), one = cmk<V>(1, 0), mone = cmk<V>(-1, 0);
+        if (p == 1) apply1(q, z, one, one, z);
+        else if (p == 2) apply1(q, z, cmk<V>(0, -1), cmk<V>(0, 1), z);
+        else apply1(q, one, z, z, mone);
+    }
+
+    // ---- one-sided Jacobi on the columns of X (rows x cols, leading dimension ld) ---------------
+    __device__ bool jacobi(V* X, int rows, int cols, int ld) {
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        constexpr int NW = NT / 32;
+        const R eps = sizeof(R) == 4 ? (R)FLT_EPSILON : (R)DBL_EPSILON;
+        const R tol = (R)4 * eps * sqrt((R)rows);
+        const int half = cols / 2, cm1 = cols - 1;
+        for (int sweep = 0; sweep < P.sweep_cap; ++sweep) {
+            int rotated = 0;
+            for (int k = 0; k < cm1; ++k) {
+                for (int pr = wid; pr < half; pr += NW) {
+                    const int sa = pr, sb = cols - 1 - pr;
+                    const int ca = sa == 0 ? 0 : 1 + (sa - 1 + k) % cm1;
+                    const int cb = 1 + (sb - 1 + k) % cm1;
+                    V* a = X + (size_t)ca * ld;
+                    V* b = X + (size_t)cb * ld;
+                    R al = 0, be = 0, gr = 0, gi = 0;
+                    for (int i = lane; i < rows; i += 32) {
+                        const V x = a[i], y = b[i];
+                        al = fma(x.x, x.x, fma(x.y, x.y, al));
+                        be = fma(y.x, y.x, fma(y.y, y.y, be));
+                        gr = fma(x.x, y.x, fma(x.y, y.y, gr));
+                        gi = fma(x.x, y.y, fma(-x.y, y.x, gi));
+                    }
+                    al = warp_sum(al); be = warp_sum(be); gr = warp_sum(gr); gi = warp_sum(gi);
+                    const R g = sqrt(gr * gr + gi * gi);
+                    if (g > tol * sqrt(al * be) && g > (R)0) {
+                        rotated = 1;
+                        const R zeta = (be - al) / (2 * g);
+                        const R t = (zeta >= 0 ? (R)1 : (R)-1) / (fabs(zeta) + sqrt((R)1 + zeta * zeta));
+                        const R c = (R)1 / sqrt((R)1 + t * t), s = c * t;
+                        const R er = gr / g, ei = gi / g;
+                        for (int i = lane; i < rows; i += 32) {
+                            const V x = a[i], y = b[i];
+                            const R emx = er * y.x + ei * y.y, emy = er * y.y - ei * y.x;  // e^{-i phi} y
+                            const R epx = er * x.x - ei * x.y, epy = er * x.y + ei * x.x;  // e^{+i phi} x
+                            a[i] = cmk<V>(c * x.x - s * emx, c * x.y - s * emy);
+                            b[i] = cmk<V>(s * epx + c * y.x, s * epy + c * y.y);
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+            if (!__syncthreads_or(rotated)) return true;
+        }
+        return false;
+    }
+
+    // ---- two-site update on (q, q+1) -----------------------------------------------------------
+    __device__ void update(int q, const V* g, bool right) {
+        const int cl = S.dims[q], cm = S.dims[q + 1], cr = S.dims[q + 2];
+        const int m = 2 * cl, n = 2 * cr;
+        const int rows = right ? m : n, cols = right ? n : m;
+        const int ld = rows + 1;
+        V* X = ((uint64_t)ld * cols <= P.x_smem) ? S.X : xg;
+        const V* A = site(q);
+        const V* B = site(q + 1);
+        // theta'[(l,s),(t,r)] = sum_{s',t'} g[(s,t),(s',t')] sum_k A[l,s',k] B[k,t',r]
+        for (int e = threadIdx.x; e < cl * cr; e += NT) {
+            const int l = e / cr, r = e - l * cr;
+            V th[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) th[u] = cmk<V>(0, 0);
+            const V* a0 = A + (l * 2) * cm;
+            const V* a1 = a0 + cm;
+            for (int k = 0; k < cm; ++k) {
+                const V x0 = a0[k], x1 = a1[k];
+                const V y0 = B[(size_t)k * n + r], y1 = B[(size_t)k * n + cr + r];
+                th[0] = cfma(x0, y0, th[0]);
+                th[1] = cfma(x0, y1, th[1]);
+                th[2] = cfma(x1, y0, th[2]);
+                th[3] = cfma(x1, y1, th[3]);
+            }
+#pragma unroll
+            for (int st = 0; st < 4; ++st) {
+                V v = cmk<V>(0, 0);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) v = cfma(g[st * 4 + u], th[u], v);
+                const int i = l * 2 + (st >> 1), j = (st & 1) * cr + r;
+                tcopy[(size_t)i * n + j] = v;
+                if (right) X[(size_t)j * ld + i] = v;
+                else X[(size_t)i * ld + j] = cmk<V>(v.x, -v.y);
+            }
+        }
+        __syncthreads();
+        if (!jacobi(X, rows, cols, ld)) {
+            status = QC_ENOCONV;
+            return;
+        }
+        // singular values: column norms, then descending order (ties: lower index first)
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        for (int j = wid; j < cols; j += NT / 32) {
+            const V* col = X + (size_t)j * ld;
+            R s = 0;
+            for (int i = lane; i < rows; i += 32) s = fma(col[i].x, col[i].x, fma(col[i].y, col[i].y, s));
+            s = warp_sum(s);
+            if (lane == 0) S.sig2[j] = s;
+        }
+        __syncthreads();
+        for (int j = threadIdx.x; j < cols; j += NT) {
+            const R sj = S.sig2[j];
+            int rk = 0;
+            for (int k = 0; k < cols; ++k) {
+                const R sk = S.sig2[k];
+                rk += (sk > sj) || (sk == sj && k < j);
+            }
+            S.perm[rk] = j;
+        }
+        __syncthreads();
+        // truncation rule, FP64: smallest r >= 1 with discarded tail <= cutoff * total, r <= chi_max
+        if (threadIdx.x == 0) {
+            double tot = 0;
+            for (int k = 0; k < cols; ++k) tot += (double)S.sig2[k];
+            const double thr = P.cutoff * tot;
+            int r = cols;
+            double tail = 0;
+            while (r > 1 && tail + (double)S.sig2[S.perm[r - 1]] <= thr) {
+                tail += (double)S.sig2[S.perm[r - 1]];
+                --r;
+            }
+            while (r > P.chi_max) {
+                tail += (double)S.sig2[S.perm[r - 1]];
+                --r;
+            }
+            double kept = 0;
+            for (int k = 0; k < r; ++k) kept += (double)S.sig2[S.perm[k]];
+            int dg = 0;
+            if (r < cols) {
+                const double sa = sqrt((double)S.sig2[S.perm[r - 1]]), sb = sqrt((double)S.sig2[S.perm[r]]);
+                dg = (sb > 0 && sa / sb - 1.0 < 1e-8);
+            }
+            S.red[40] = tot > 0 ? tail / tot : 0.0;
+            S.red[41] = kept > 0 ? 1.0 / sqrt(kept) : 0.0;
+            S.red[42] = (double)r;
+            S.red[43] = (double)dg;
+        }
+        __syncthreads();
+        const int r = (int)S.red[42];
+        disc += S.red[40];
+        degen += (int)S.red[43];
+        const R scale = (R)S.red[41];
+        if (r > P.cap[q + 1]) {
+            status = QC_ECAPACITY;
+            return;
+        }
+        // normalise the kept columns to unit length (the orthonormal factor)
+        for (int e = threadIdx.x; e < r * rows; e += NT) {
+            const int k = e / rows, i = e - k * rows;
+            const int j = S.perm[k];
+            const R sg = S.sig2[j];
+            const R inv = sg > (R)0 ? (R)1 / sqrt(sg) : (R)0;
+            V* col = X + (size_t)j * ld;
+            col[i] = cmk<V>(col[i].x * inv, col[i].y * inv);
+        }
+        __syncthreads();
+        V* As = site(q);
+        V* Bs = site(q + 1);
+        if (right) {
+            // A[q] = U (cl, 2, r);  A[q+1] = scale * U^H theta' (r, 2, cr)
+            for (int e = threadIdx.x; e < m * r; e += NT) {
+                const int i = e / r, k = e - i * r;
+                As[e] = X[(size_t)S.perm[k] * ld + i];
+            }
+            for (int e = threadIdx.x; e < r * n; e += NT) {
+                const int k = e / n, j = e - k * n;
+                const V* u = X + (size_t)S.perm[k] * ld;
+                V acc = cmk<V>(0, 0);
+                for (int i = 0; i < m; ++i) acc = cfmac(u[i], tcopy[(size_t)i * n + j], acc);
+                Bs[e] = cmk<V>(acc.x * scale, acc.y * scale);
+            }
+        } else {
+            // A[q+1] = U'^H (r, 2, cr);  A[q] = scale * theta' U' (cl, 2, r)
+            for (int e = threadIdx.x; e < r * n; e += NT) {
+                const int k = e / n, j = e - k * n;
+                const V u = X[(size_t)S.perm[k] * ld + j];
+                Bs[e] = cmk<V>(u.x, -u.y);
+            }
+            for (int e = threadIdx.x; e < m * r; e += NT) {
+                const int i = e / r, k = e - i * r;
+                const V* u = X + (size_t)S.perm[k] * ld;
+                V acc = cmk<V>(0, 0);
+                for (int j = 0; j < n; ++j) acc = cfma(tcopy[(size_t)i * n + j], u[j], acc);
+                As[e] = cmk<V>(acc.x * scale, acc.y * scale);
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) S.dims[q + 1] = r;
+        __syncthreads();
+        chi_peak = max(chi_peak, r);
+        ++nupd;
+    }
+
+    // ---- readout on site q (the orthogonality centre) ------------------------------------------
+    // returns the outcome, or -1 when the shot ends (rejected / error)
+    __device__ int readout(int q, uint32_t rid, bool is_meas, uint64_t shot, int64_t src) {
+        const int cl = S.dims[q], cr = S.dims[q + 1];
+        V* a = site(q);
+        double p0 = 0, p1 = 0;
+        for (int e = threadIdx.x; e < cl * cr; e += NT) {
+            const int l = e / cr, r = e - l * cr;
+            const V x = a[(l * 2) * cr + r], y = a[(l * 2 + 1) * cr + r];
+            p0 += (double)x.x * x.x + (double)x.y * x.y;
+            p1 += (double)y.x * y.x + (double)y.y * y.y;
+        }
+        p0 = block_sum<NT>(p0, S.red);
+        p1 = block_sum<NT>(p1, S.red);
+        const double tot = p0 + p1;
+        const double pr1 = tot > 0 ? p1 / tot : 0.0;
+        int outcome;
+        if (P.reference) {
+            if (is_meas) {
+                const double lim = P.precision == QC_C128 ? 1e-10 : 1e-5;
+                if (pr1 > lim) {
+                    if (threadIdx.x == 0) atomicCAS(P.ref_status, 0, (int)(src + 1));
+                }
+                outcome = 0;
+            } else {
+                outcome = pr1 > 0.5 ? 1 : 0;
+            }
+        } else {
+            const double u = readout_uniform(rid, shot, P.k0, P.k1);
+            outcome = u < pr1 ? 1 : 0;
+        }
+        if (is_meas && outcome == 1) {
+            status = 1;
+            abort_op = src;
+            return -1;
+        }
+        const double po = outcome ? p1 : p0;
+        if (!(po > 0)) {  // projection onto a zero-probability branch cannot happen for draws
+            status = QC_EINVAL;
+            return -1;
+        }
+        const R sc = (R)(1.0 / sqrt(po));
+        const bool flip = (!is_meas) && outcome == 1;  // reset to |0>: project on 1 then X
+        for (int e = threadIdx.x; e < cl * cr; e += NT) {
+            const int l = e / cr, r = e - l * cr;
+            V* x0 = a + (l * 2) * cr + r;
+            V* x1 = x0 + cr;
+            const V keep = outcome ? *x1 : *x0;
+            const V kv = cmk<V>(keep.x * sc, keep.y * sc);
+            if (outcome == 0) { *x0 = kv; *x1 = cmk<V>(0, 0); }
+            else if (flip) { *x0 = kv; *x1 = cmk<V>(0, 0); }
+            else { *x0 = cmk<V>(0, 0); *x1 = kv; }
+        }
+        __syncthreads();
+        return outcome;
+    }
+
+    // ---- <ref|psi> by a transfer sweep ----------------------------------------------------------
+    __device__ double2 overlap_ref() {
+        // E: (chi_ref x chi), T1: (chi_ref x 2 x chi); placed in shared X when it fits
+        const int cap2 = P.chi_max;  // upper bound of any bond
+        const uint64_t need = (uint64_t)cap2 * cap2 * 3;
+        V* E = (need <= P.x_smem) ? S.X : xg;
+        V* T1 = E + (size_t)cap2 * cap2;
+        if (threadIdx.x == 0) E[0] = cmk<V>(1, 0);
+        __syncthreads();
+        const V* refsite = P.ref;
+        for (int q = 0; q < P.nq; ++q) {
+            const int ca = P.ref_dims[q], ca2 = P.ref_dims[q + 1];
+            const int cb = S.dims[q], cb2 = S.dims[q + 1];
+            const V* Aq = site(q);
+            const V* Rq = refsite + P.off[q];
+            // T1[a][s][b'] = sum_b E[a][b] A[b][s][b']
+            for (int e = threadIdx.x; e < ca * 2 * cb2; e += NT) {
+                const int a_ = e / (2 * cb2), rest = e - a_ * 2 * cb2;
+                V acc = cmk<V>(0, 0);
+                for (int b = 0; b < cb; ++b) acc = cfma(E[(size_t)a_ * cb + b], Aq[(size_t)b * 2 * cb2 + rest], acc);
+                T1[e] = acc;
+            }
+            __syncthreads();
+            // E'[a'][b'] = sum_{a,s} conj(R[a][s][a']) T1[a][s][b']
+            for (int e = threadIdx.x; e < ca2 * cb2; e += NT) {
+                const int ap = e / cb2, bp = e - ap * cb2;
+                V acc = cmk<V>(0, 0);
+                for (int a_ = 0; a_ < ca; ++a_)
+                    for (int s = 0; s < 2; ++s)
+                        acc = cfmac(Rq[((size_t)a_ * 2 + s) * ca2 + ap], T1[((size_t)a_ * 2 + s) * cb2 + bp], acc);
+                E[e] = acc;
+            }
+            __syncthreads();
+        }
+        const V ov = E[0];
+        __syncthreads();
+        return make_double2((double)ov.x, (double)ov.y);
+    }
+
+    __device__ double centre_norm2(const V* base, const int* dims) {
+        const int q = P.final_center;
+        const int cl = dims[q], cr = dims[q + 1];
+        const V* a = base + P.off[q];
+        double s = 0;
+        for (int e = threadIdx.x; e < cl * 2 * cr; e += NT) s += (double)a[e].x * a[e].x + (double)a[e].y * a[e].y;
+        return block_sum<NT>(s, S.red);
+    }
+
+    // ---- faults of one shot into S.fch / S.fcode (sorted by channel); returns the count ------
+    __device__ int faults(uint64_t shot) {
+        __shared__ int nf;
+        if (threadIdx.x == 0) nf = 0;
+        __syncthreads();
+        if (P.reference) return 0;
+        if (P.weight < 0) {
+            const uint32_t w = (uint32_t)(shot >> 6), lane = (uint32_t)(shot & 63);
+            const uint32_t ng = (P.nchan + 3) / 4;
+            for (uint32_t g = threadIdx.x; g < ng; g += NT) {
+                const U4 u = philox(g, w, 0, TAG_WORD, P.k0, P.k1);
+#pragma unroll
+                for (uint32_t j = 0; j < 4; ++j) {
+                    const uint32_t c = g * 4 + j;
+                    const uint32_t u0 = u4_get(u, j);
+                    if (c >= P.nchan || u0 >= P.tg[63]) continue;
+                    const uint64_t msk = lane_mask(u0, c, w, P.tg, P.k0, P.k1);
+                    if (!((msk >> lane) & 1)) continue;
+                    const int slot_i = atomicAdd(&nf, 1);
+                    if (slot_i < MAXF) {
+                        S.fch[slot_i] = c;
+                        S.fcode[slot_i] = (uint8_t)fault_code(P.chan_kind[c], c, w, lane, P.k0, P.k1);
+                    }
+                }
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {  // insertion sort by channel
+                const int cnt = min(nf, MAXF);
+                for (int i = 1; i < cnt; ++i) {
+                    const uint32_t c = S.fch[i];
+                    const uint8_t d = S.fcode[i];
+                    int k = i;
+                    while (k > 0 && S.fch[k - 1] > c) { S.fch[k] = S.fch[k - 1]; S.fcode[k] = S.fcode[k - 1]; --k; }
+                    S.fch[k] = c;
+                    S.fcode[k] = d;
+                }
+            }
+        } else if (threadIdx.x == 0) {
+            uint32_t draw = 0;
+            const uint32_t M = P.nchan, W = (uint32_t)P.weight;
+            int cnt = 0;
+            for (uint32_t j = M - W; j < M; ++j) {
+                const uint32_t t = exact_bounded(shot, draw, j + 1, P.k0, P.k1);
+                bool present = false;
+                for (int k = 0; k < cnt; ++k) present |= (S.fch[k] == t);
+                const uint32_t v = present ? j : t;
+                if (cnt < MAXF) {
+                    int k = cnt;
+                    while (k > 0 && S.fch[k - 1] > v) { S.fch[k] = S.fch[k - 1]; --k; }
+                    S.fch[k] = v;
+                }
+                ++cnt;
+            }
+            for (int k = 0; k < min(cnt, MAXF); ++k) S.fcode[k] = (uint8_t)exact_code(P.chan_kind[S.fch[k]], S.fch[k], shot, P.k0, P.k1);
+            nf = cnt;
+        }
+        __syncthreads();
+        const int out = nf;
+        __syncthreads();
+        return out;
+    }
+
+    __device__ void run(uint64_t task) {
+        const uint64_t shot = P.reference ? 0 : P.shots[task];
+        status = 0; disc = 0; degen = 0; chi_peak = 1; nupd = 0; abort_op = -1;
+        for (int q = threadIdx.x; q <= P.nq; q += NT) S.dims[q] = 1;
+        for (int q = threadIdx.x; q < P.nq; q += NT) {
+            V* a = site(q);
+            a[0] = cmk<V>(1, 0);
+            a[1] = cmk<V>(0, 0);
+        }
+        __syncthreads();
+        const int nf = faults(shot);
+        if (nf > MAXF) status = QC_ECAPACITY;
+        int fptr = 0;
+        for (uint32_t base = 0; base < P.nops && status == 0; base += OPCH) {
+            const uint32_t cnt = min((uint32_t)OPCH, P.nops - base);
+            for (uint32_t i = threadIdx.x; i < cnt; i += NT) S.ops[i] = P.prog[base + i];
+            __syncthreads();
+            for (uint32_t i = 0; i < cnt && status == 0; ++i) {
+                const MpsOp op = S.ops[i];
+                switch (op.kind) {
+                    case M_G1: {
+                        const V* g = P.g1 + op.a * 4;
+                        apply1(op.q, g[0], g[1], g[2], g[3]);
+                        break;
+                    }
+                    case M_CH1:
+                    case M_CH2: {
+                        if (fptr < nf && S.fch[fptr] == op.a) {
+                            const uint32_t code = S.fcode[fptr];
+                            ++fptr;
+                            if (op.kind == M_CH1) apply_pauli(op.q, code);
+                            else { apply_pauli(op.q, code >> 2); apply_pauli(op.b, code & 3); }
+                        }
+                        break;
+                    }
+                    case M_G2:
+                        update(op.q, P.g4 + op.a * 16, (op.flags & F_CENTER_RIGHT) != 0);
+                        if (status != 0) abort_op = op.src;
+                        break;
+                    case M_MEAS:
+                    case M_RESET:
+                        readout(op.q, op.a, op.kind == M_MEAS, shot, op.src);
+                        break;
+                    default: break;
+                }
+            }
+            __syncthreads();
+        }
+        // finish
+        double fid = -1.0;
+        int lerr = 0;
+        if (status == 0 && !P.reference) {
+            const double2 ov = overlap_ref();
+            const double nn = centre_norm2(slot, S.dims);
+            const double ov2 = ov.x * ov.x + ov.y * ov.y;
+            fid = (nn > 0 && P.ref_norm > 0) ? ov2 / (nn * P.ref_norm) : 0.0;
+            double tau = P.tau;
+            if (!(tau > 0)) tau = P.precision == QC_C128 ? 1e-8 : fmax(1e-3, 10.0 * (P.ref_disc + disc));
+            lerr = (1.0 - fid) > tau;
+        }
+        if (threadIdx.x == 0) {
+            if (P.reference) {
+                for (int q = 0; q <= P.nq; ++q) P.ref_dims_out[q] = S.dims[q];
+                *P.ref_disc_out = disc;
+                if (status != 0) atomicCAS(P.ref_status, 0, -1000 + status);
+            } else {
+                const int wb = min(nf, P.wmax);
+                atomicAdd(&P.counts[3 * wb + 0], 1ull);
+                if (status == 0) {
+                    atomicAdd(&P.counts[3 * wb + 1], 1ull);
+                    if (lerr) atomicAdd(&P.counts[3 * wb + 2], 1ull);
+                }
+                if (P.per_shot) {
+                    qc_shot_result res;
+                    res.shot = shot;
+                    res.status = status;
+                    res.weight = nf;
+                    res.logical_error = lerr;
+                    res.chi_peak = chi_peak;
+                    res.abort_op = abort_op;
+                    res.fidelity = fid;
+                    res.discarded = disc;
+                    res.degenerate_cuts = degen;
+                    res.n_updates = nupd;
+                    P.per_shot[task] = res;
+                }
+            }
+        }
+        __syncthreads();
+    }
+};
+
+template <typename R, int NT>
+__global__ void __launch_bounds__(NT, 1) engine_kernel(const EngineParams<R> P) {
+    using V = typename VecOf<R>::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Shared<R> S;
+    unsigned char* p = smem_raw;
+    S.X = reinterpret_cast<V*>(p); p += (size_t)P.x_smem * sizeof(V);
+    S.ops = reinterpret_cast<MpsOp*>(p); p += OPCH * sizeof(MpsOp);
+    S.red = reinterpret_cast<double*>(p); p += 64 * sizeof(double);
+    S.sig2 = reinterpret_cast<R*>(p); p += (size_t)2 * P.chi_max * sizeof(R) + 16;
+    S.perm = reinterpret_cast<int*>(p); p += (size_t)2 * P.chi_max * sizeof(int);
+    S.dims = reinterpret_cast<int*>(p); p += (size_t)(P.nq + 1) * sizeof(int);
+    S.fch = reinterpret_cast<uint32_t*>(p); p += MAXF * sizeof(uint32_t);
+    S.fcode = reinterpret_cast<uint8_t*>(p);
+
+    Engine<R, NT> eng(P, S, blockIdx.x);
+    __shared__ unsigned long long task_s;
+    for (;;) {
+        if (threadIdx.x == 0) task_s = atomicAdd(P.next_task, 1ull);
+        __syncthreads();
+        const unsigned long long task = task_s;
+        __syncthreads();
+        if (task >= P.ntasks) break;
+        eng.run(task);
+    }
+}
+
+template <typename R, int NT>
+size_t engine_smem(const EngineParams<R>& P) {
+    using V = typename VecOf<R>::T;
+    return (size_t)P.x_smem * sizeof(V) + OPCH * sizeof(MpsOp) + 64 * sizeof(double) +
+           (size_t)2 * P.chi_max * sizeof(R) + 16 + (size_t)2 * P.chi_max * sizeof(int) +
+           (size_t)(P.nq + 1) * sizeof(int) + MAXF * sizeof(uint32_t) + MAXF + 16;
+}
+
+// ---- gate tables ------------------------------------------------------------------------------
+void gate_tables(std::vector<double2>& g1, std::vector<double2>& g4) {
+    const double h = std::sqrt(0.5), c8 = std::cos(M_PI / 4), s8 = std::sin(M_PI / 4);
+    g1.assign(G1_COUNT * 4, make_double2(0, 0));
+    auto set1 = [&](int gi, double2 a, double2 b, double2 c, double2 d) {
+        g1[gi * 4 + 0] = a; g1[gi * 4 + 1] = b; g1[gi * 4 + 2] = c; g1[gi * 4 + 3] = d;
+    };
+    const double2 z = make_double2(0, 0), o = make_double2(1, 0);
+    set1(G1_H, make_double2(h, 0), make_double2(h, 0), make_double2(h, 0), make_double2(-h, 0));
+    set1(G1_S, o, z, z, make_double2(0, 1));
+    set1(G1_SDG, o, z, z, make_double2(0, -1));
+    set1(G1_X, z, o, o, z);
+    set1(G1_Y, z, make_double2(0, -1), make_double2(0, 1), z);
+    set1(G1_Z, o, z, z, make_double2(-1, 0));
+    set1(G1_T, o, z, z, make_double2(c8, s8));
+    set1(G1_TDG, o, z, z, make_double2(c8, -s8));
+    g4.assign(G4_COUNT * 16, z);
+    auto set4 = [&](int gi, int row, int col, double2 v) { g4[gi * 16 + row * 4 + col] = v; };
+    // index (s,t) = 2*s + t with s the site q (high bit)
+    // CX control high, target low: |s t> -> |s, t^s>
+    for (int s = 0; s < 2; ++s)
+        for (int t = 0; t < 2; ++t) set4(G4_CX_HL, 2 * s + (t ^ s), 2 * s + t, o);
+    // CX control low, target high
+    for (int s = 0; s < 2; ++s)
+        for (int t = 0; t < 2; ++t) set4(G4_CX_LH, 2 * (s ^ t) + t, 2 * s + t, o);
+    for (int k = 0; k < 4; ++k) set4(G4_CZ, k, k, k == 3 ? make_double2(-1, 0) : o);
+    for (int s = 0; s < 2; ++s)
+        for (int t = 0; t < 2; ++t) set4(G4_SWAP, 2 * t + s, 2 * s + t, o);
+    for (int k = 0; k < 4; ++k) set4(G4_ID, k, k, o);
+}
+
+struct DeviceTables {
+    double2* g1d = nullptr;
+    double2* g4d = nullptr;
+    float2* g1f = nullptr;
+    float2* g4f = nullptr;
+};
+
+std::mutex g_tab_mu;
+std::map<int, DeviceTables> g_tables;
+
+qc_status device_tables(DeviceTables** out) {
+    int d = 0;
+    QC_CUDA(cudaGetDevice(&d));
+    std::lock_guard<std::mutex> lk(g_tab_mu);
+    auto it = g_tables.find(d);
+    if (it == g_tables.end()) {
+        std::vector<double2> g1, g4;
+        gate_tables(g1, g4);
+        std::vector<float2> f1(g1.size()), f4(g4.size());
+        for (size_t i = 0; i < g1.size(); ++i) f1[i] = make_float2((float)g1[i].x, (float)g1[i].y);
+        for (size_t i = 0; i < g4.size(); ++i) f4[i] = make_float2((float)g4[i].x, (float)g4[i].y);
+        DeviceTables t;
+        QC_CUDA(cudaMalloc(&t.g1d, g1.size() * sizeof(double2)));
+        QC_CUDA(cudaMalloc(&t.g4d, g4.size() * sizeof(double2)));
+        QC_CUDA(cudaMalloc(&t.g1f, f1.size() * sizeof(float2)));
+        QC_CUDA(cudaMalloc(&t.g4f, f4.size() * sizeof(float2)));
+        QC_CUDA(cudaMemcpy(t.g1d, g1.data(), g1.size() * sizeof(double2), cudaMemcpyHostToDevice));
+        QC_CUDA(cudaMemcpy(t.g4d, g4.data(), g4.size() * sizeof(double2), cudaMemcpyHostToDevice));
+        QC_CUDA(cudaMemcpy(t.g1f, f1.data(), f1.size() * sizeof(float2), cudaMemcpyHostToDevice));
+        QC_CUDA(cudaMemcpy(t.g4f, f4.data(), f4.size() * sizeof(float2), cudaMemcpyHostToDevice));
+        it = g_tables.emplace(d, t).first;
+    }
+    *out = &it->second;
+    return QC_OK;
+}
+
+constexpr int NT_F = 512;
+constexpr int NT_D = 256;
+constexpr size_t SMEM_BUDGET = 200 * 1024;
+
+}  // namespace
+
+// Layout of one slot: bond capacities and site offsets.
+struct SlotLayout {
+    std::vector<int> cap;
+    std::vector<uint64_t> off;
+    int chi_cap;
+    uint64_t stride;
+};
+
+static SlotLayout slot_layout(int n, int chi_max) {
+    SlotLayout L;
+    L.cap.assign(n + 1, 1);
+    L.chi_cap = 1;
+    for (int k = 1; k < n; ++k) {
+        const int e = std::min(k, n - k);
+        const int64_t full = e >= 30 ? (int64_t)1 << 30 : (int64_t)1 << e;
+        L.cap[k] = (int)std::min<int64_t>(full, chi_max);
+        L.chi_cap = std::max(L.chi_cap, L.cap[k]);
+    }
+    L.off.assign(n + 1, 0);
+    for (int q = 0; q < n; ++q) L.off[q + 1] = L.off[q] + (uint64_t)L.cap[q] * 2 * L.cap[q + 1];
+    L.stride = (L.off[n] + 1) & ~1ull;
+    return L;
+}
+
+// Host driver shared by mps_sample_batch and the serving loop.
+template <typename R, int NT>
+static qc_status run_engine(CircuitImpl& c, qc_noise noise, const uint64_t* shots_dev, uint64_t nshots,
+                            qc_mps_params prm, unsigned long long* counts_dev, int wmax,
+                            qc_shot_result* per_shot, cudaStream_t s, int max_slots) {
+    using V = typename VecOf<R>::T;
+    DeviceCopy* dc;
+    qc_status st = c.device_copy(&dc);
+    if (st != QC_OK) return st;
+    DeviceTables* tabs;
+    st = device_tables(&tabs);
+    if (st != QC_OK) return st;
+    const SlotLayout L = slot_layout(c.n, prm.chi_max);
+    const int chi = L.chi_cap;
+    // X in shared memory up to the budget
+    const uint64_t x_full = (uint64_t)(2 * chi + 1) * (2 * chi);
+    const uint64_t over_full = (uint64_t)chi * chi * 3;
+    EngineParams<R> P{};
+    P.chi_max = chi;
+    uint64_t fixed = engine_smem<R, NT>(P) + (uint64_t)(c.n + 1) * sizeof(int);
+    uint64_t x_cap = (SMEM_BUDGET - std::min<uint64_t>(SMEM_BUDGET, fixed)) / sizeof(V);
+    x_cap = std::min<uint64_t>(x_cap, std::max(x_full, over_full));
+    const uint64_t xg_elems = std::max(x_full, over_full);
+    const uint64_t scratch_stride = xg_elems + (uint64_t)(2 * chi) * (2 * chi);
+
+    int dev = 0, nsm = 0;
+    QC_CUDA(cudaGetDevice(&dev));
+    QC_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+
+    P.prog = dc->mps;
+    P.nops = (uint32_t)c.mps.size();
+    P.nq = c.n;
+    P.chan_kind = dc->chan_kind;
+    P.nchan = (uint32_t)c.chan_kind.size();
+    P.g1 = reinterpret_cast<const V*>(sizeof(R) == 4 ? (const void*)tabs->g1f : (const void*)tabs->g1d);
+    P.g4 = reinterpret_cast<const V*>(sizeof(R) == 4 ? (const void*)tabs->g4f : (const void*)tabs->g4d);
+    P.slot_stride = L.stride;
+    P.scratch_stride = scratch_stride;
+    P.xg_elems = xg_elems;
+    P.x_smem = (uint32_t)x_cap;
+    P.cutoff = prm.cutoff;
+    P.k0 = (uint32_t)noise.seed;
+    P.k1 = (uint32_t)(noise.seed >> 32);
+    const Thresholds th = make_thresholds(noise.p);
+    for (int i = 0; i < 64; ++i) P.tg[i] = th.tg[i];
+    P.weight = noise.fault_weight;
+    P.tau = prm.tau;
+    P.precision = prm.precision;
+    P.wmax = wmax;
+    P.sweep_cap = sizeof(R) == 4 ? 40 : 60;
+    // final orthogonality centre of the program
+    {
+        int center = 0;
+        for (const MpsOp& o : c.mps) {
+            if (o.kind == M_G2) center = (o.flags & F_CENTER_RIGHT) ? o.q + 1 : o.q;
+            else if (o.kind == M_MEAS || o.kind == M_RESET) center = o.q;
+        }
+        P.final_center = center;
+    }
+    const size_t smem = engine_smem<R, NT>(P);
+    QC_CUDA(cudaFuncSetAttribute(engine_kernel<R, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    QC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, engine_kernel<R, NT>, NT, smem));
+    if (per_sm < 1) return fail(QC_ENOMEM, "engine does not fit on an SM (smem %zu)", smem);
+    uint64_t slots = std::min<uint64_t>(nshots ? nshots : 1, (uint64_t)per_sm * nsm);
+    if (max_slots > 0) slots = std::min<uint64_t>(slots, (uint64_t)max_slots);
+    if (slots < 1) slots = 1;
+
+    // 1. the noiseless reference state, computed once per (device, chi_max, cutoff, precision)
+    RefState* ref = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(c.ref_mu);
+        const RefKey key{dev, prm.chi_max, prm.precision, prm.cutoff};
+        auto it = c.refs.find(key);
+        if (it == c.refs.end()) {
+            RefState rs;
+            char* tmp = nullptr;
+            const size_t tmp_bytes = scratch_stride * sizeof(V) + 64;
+            cudaError_t e = cudaMalloc(&rs.state, L.stride * sizeof(V));
+            if (e == cudaSuccess) e = cudaMalloc(&rs.dims, (c.n + 1) * sizeof(int));
+            if (e == cudaSuccess) e = cudaMalloc(&rs.cap, (c.n + 1) * sizeof(int));
+            if (e == cudaSuccess) e = cudaMalloc(&rs.off, (c.n + 1) * sizeof(uint64_t));
+            if (e == cudaSuccess) e = cudaMalloc(&tmp, tmp_bytes);
+            if (e == cudaSuccess) e = cudaMemcpy(rs.cap, L.cap.data(), (c.n + 1) * sizeof(int), cudaMemcpyHostToDevice);
+            if (e == cudaSuccess) e = cudaMemcpy(rs.off, L.off.data(), (c.n + 1) * sizeof(uint64_t), cudaMemcpyHostToDevice);
+            if (e == cudaSuccess) e = cudaMemset(tmp, 0, 64);
+            qc_status out = QC_OK;
+            if (e != cudaSuccess) out = cuda_fail(e, "reference workspace");
+            if (out == QC_OK) {
+                EngineParams<R> Pr = P;
+                Pr.reference = 1;
+                Pr.mps = reinterpret_cast<V*>(rs.state);
+                Pr.off = rs.off;
+                Pr.cap = rs.cap;
+                Pr.scratch = reinterpret_cast<V*>(tmp + 64);
+                Pr.ntasks = 1;
+                Pr.next_task = reinterpret_cast<unsigned long long*>(tmp);
+                Pr.ref_status = reinterpret_cast<int*>(tmp + 8);
+                Pr.ref_disc_out = reinterpret_cast<double*>(tmp + 16);
+                Pr.ref_dims_out = rs.dims;
+                Pr.counts = nullptr;
+                engine_kernel<R, NT><<<1, NT, smem, s>>>(Pr);
+                e = cudaGetLastError();
+                int st_h = 0;
+                if (e == cudaSuccess) e = cudaMemcpyAsync(&st_h, Pr.ref_status, sizeof(int), cudaMemcpyDeviceToHost, s);
+                if (e == cudaSuccess) e = cudaMemcpyAsync(&rs.disc, Pr.ref_disc_out, sizeof(double), cudaMemcpyDeviceToHost, s);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+                if (e != cudaSuccess) out = cuda_fail(e, "reference run");
+                else if (st_h > 0) out = fail(QC_EINVAL, "measurement at instruction %d is not deterministically 0 in the noiseless circuit", st_h - 1);
+                else if (st_h < 0) out = fail((qc_status)(st_h + 1000), "reference run failed (status %d)", st_h + 1000);
+                if (out == QC_OK) {
+                    const int q = P.final_center;
+                    std::vector<int> rd(c.n + 1);
+                    e = cudaMemcpy(rd.data(), rs.dims, rd.size() * sizeof(int), cudaMemcpyDeviceToHost);
+                    std::vector<V> cen;
+                    if (e == cudaSuccess) {
+                        cen.resize((size_t)rd[q] * 2 * rd[q + 1]);
+                        e = cudaMemcpy(cen.data(), reinterpret_cast<V*>(rs.state) + L.off[q], cen.size() * sizeof(V),
+                                       cudaMemcpyDeviceToHost);
+                    }
+                    if (e != cudaSuccess) out = cuda_fail(e, "reference centre");
+                    double nn = 0;
+                    for (const V& v : cen) nn += (double)v.x * v.x + (double)v.y * v.y;
+                    rs.norm = nn;
+                }
+            }
+            cudaFree(tmp);
+            if (out != QC_OK) {
+                cudaFree(rs.state); cudaFree(rs.dims); cudaFree(rs.cap); cudaFree(rs.off);
+                return out;
+            }
+            it = c.refs.emplace(key, rs).first;
+        }
+        ref = &it->second;
+    }
+    if (nshots == 0) return QC_OK;
+
+    // 2. the shots: slots' site tensors and split scratch
+    const uint64_t mps_elems = slots * L.stride;
+    const uint64_t scr_elems = slots * scratch_stride;
+    char* ws = nullptr;
+    const size_t bytes = (mps_elems + scr_elems) * sizeof(V) + 64;
+    cudaError_t e = cudaMallocAsync((void**)&ws, bytes, s);
+    if (e != cudaSuccess) return fail(QC_ENOMEM, "workspace of %zu bytes: %s", bytes, cudaGetErrorString(e));
+    qc_status out = QC_OK;
+    do {
+        V* mps = reinterpret_cast<V*>(ws + 64);
+        V* scr = mps + mps_elems;
+        e = cudaMemsetAsync(ws, 0, 64, s);
+        if (e != cudaSuccess) { out = cuda_fail(e, "workspace init"); break; }
+        P.reference = 0;
+        P.mps = mps;
+        P.off = ref->off;
+        P.cap = ref->cap;
+        P.scratch = scr;
+        P.ref = reinterpret_cast<const V*>(ref->state);
+        P.ref_dims = ref->dims;
+        P.ref_disc = ref->disc;
+        P.ref_norm = ref->norm;
+        P.shots = shots_dev;
+        P.ntasks = nshots;
+        P.next_task = reinterpret_cast<unsigned long long*>(ws);
+        P.per_shot = per_shot;
+        P.counts = counts_dev;
+        engine_kernel<R, NT><<<(unsigned)slots, NT, smem, s>>>(P);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) { out = cuda_fail(e, "engine"); break; }
+    } while (0);
+    cudaFreeAsync(ws, s);
+    return out;
+}
+
+qc_status engine_launch(CircuitImpl& c, qc_noise noise, const uint64_t* shots_dev, uint64_t nshots,
+                        qc_mps_params prm, unsigned long long* counts_dev, int wmax, qc_shot_result* per_shot,
+                        cudaStream_t s, int max_slots) {
+    if (!(noise.p >= 0.0 && noise.p < 1.0)) return fail(QC_EINVAL, "p must lie in [0, 1)");
+    if (prm.chi_max < 1) return fail(QC_EINVAL, "chi_max must be >= 1");
+    if (!(prm.cutoff >= 0.0)) return fail(QC_EINVAL, "cutoff must be >= 0");
+    if (prm.precision != QC_C64 && prm.precision != QC_C128) return fail(QC_EINVAL, "unknown precision");
+    if (noise.fault_weight >= 0 && (uint64_t)noise.fault_weight > c.chan_kind.size())
+        return fail(QC_EINVAL, "fault weight exceeds the number of channels");
+    if (noise.fault_weight > MAXF) return fail(QC_EINVAL, "fault weight above %d", MAXF);
+    if (nshots && !shots_dev) return fail(QC_EINVAL, "null shots");
+    if (c.n < 2) return fail(QC_EINVAL, "the MPS engine needs at least two qubits");
+    if (prm.precision == QC_C64)
+        return run_engine<float, NT_F>(c, noise, shots_dev, nshots, prm, counts_dev, wmax, per_shot, s, max_slots);
+    return run_engine<double, NT_D>(c, noise, shots_dev, nshots, prm, counts_dev, wmax, per_shot, s, max_slots);
+}
+
+qc_status shot_footprint(const CircuitImpl& c, qc_mps_params prm, uint64_t* bytes) {
+    const SlotLayout L = slot_layout(c.n, std::max(1, prm.chi_max));
+    const int chi = L.chi_cap;
+    const uint64_t x_full = std::max((uint64_t)(2 * chi + 1) * (2 * chi), (uint64_t)chi * chi * 3);
+    const uint64_t scratch = x_full + (uint64_t)(2 * chi) * (2 * chi);
+    const uint64_t es = prm.precision == QC_C128 ? 16 : 8;
+    *bytes = (L.stride + scratch) * es;
+    return QC_OK;
+}
+
+}  // namespace qc
+
+using namespace qc;
+
+extern "C" qc_status mps_sample_batch(const qc_circuit* circuit, qc_noise noise, const uint64_t* shots_dev,
+                                      uint64_t nshots, qc_mps_params params, qc_counts* per_w, int32_t w_max,
+                                      qc_shot_result* per_shot_dev, void* stream) {
+    if (!circuit) return fail(QC_EINVAL, "null circuit");
+    if (w_max < 0 || w_max > 4095) return fail(QC_EINVAL, "w_max must lie in [0, 4095]");
+    cudaStream_t s = (cudaStream_t)stream;
+    CircuitImpl& c = const_cast<qc_circuit*>(circuit)->impl;
+    unsigned long long* counts = nullptr;
+    const size_t cb = 3 * (size_t)(w_max + 1) * sizeof(unsigned long long);
+    QC_CUDA(cudaMallocAsync((void**)&counts, cb, s));
+    qc_status st = QC_OK;
+    cudaError_t e = cudaMemsetAsync(counts, 0, cb, s);
+    if (e != cudaSuccess) st = cuda_fail(e, "memset");
+    if (st == QC_OK) st = engine_launch(c, noise, shots_dev, nshots, params, counts, w_max, per_shot_dev, s, 0);
+    if (st == QC_OK) {
+        std::vector<unsigned long long> h(3 * (w_max + 1));
+        e = cudaMemcpyAsync(h.data(), counts, cb, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) st = cuda_fail(e, "engine");
+        if (st == QC_OK && per_w)
+            for (int w = 0; w <= w_max; ++w) {
+                per_w[w].n += h[3 * w];
+                per_w[w].n_acc += h[3 * w + 1];
+                per_w[w].n_err += h[3 * w + 2];
+            }
+    }
+    cudaFreeAsync(counts, s);
+    return st;
+}
+
+extern "C" qc_status mps_shot_footprint(const qc_circuit* circuit, qc_mps_params params, uint64_t* bytes) {
+    if (!circuit || !bytes) return fail(QC_EINVAL, "null argument");
+    return shot_footprint(circuit->impl, params, bytes);
+}

@@ -1,0 +1,280 @@
+// Serving loop: sampling jobs for different circuits and noise rates arrive while others run.
+//
+// A job is pre-screened as a whole (Sec. 4.2), then its surviving shots are cut into chunks.
+// Worker threads, one per CUDA stream, take the next chunk of any admitted job, so chunks of
+// different jobs run concurrently on the device; inside a chunk the persistent engine retires
+// rejected shots early and back-fills their slots (Sec. 4.3).  A chunk is launched only when its
+// in-flight footprint (slots x per-shot bytes) fits the HBM budget next to the chunks already
+// running; finished chunks release their share.  Latency is measured from submission to the end
+// of the job's last chunk.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <thread>
+
+#include "qc_internal.h"
+
+namespace qc {
+namespace {
+
+constexpr int WBINS = 16;
+constexpr uint64_t CHUNK_SHOTS = 2048;
+
+struct Job {
+    uint64_t id;
+    CircuitImpl* circ;
+    qc_noise noise;
+    qc_mps_params prm;
+    uint64_t shot0, nshots;
+    int state = QC_PENDING;   // QC_PENDING, QC_OK, or an error
+    bool prescreened = false, prescreening = false, cancelled = false;
+    uint64_t survivors = 0;
+    uint64_t* surv_dev = nullptr;
+    uint64_t next = 0;         // next survivor index to hand out
+    uint64_t done = 0;         // survivors finished
+    int inflight = 0;          // chunks running
+    uint64_t footprint = 0;    // bytes per in-flight shot
+    qc_counts counts[WBINS] = {};
+    double submit_ms = 0, start_ms = -1, end_ms = -1;
+};
+
+}  // namespace
+
+struct Server {
+    qc_serve_cfg cfg;
+    int device = 0;
+    int max_slots = 0;
+    std::mutex mu;
+    std::condition_variable cv;
+    std::deque<Job*> order;          // admission order
+    std::map<uint64_t, Job*> jobs;
+    uint64_t next_id = 1;
+    uint64_t inflight_bytes = 0;
+    bool stop = false;
+    std::vector<std::thread> workers;
+    std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
+
+    double now_ms() const {
+        return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    }
+
+    void finish(Job* j, int state) {
+        j->state = state;
+        j->end_ms = now_ms();
+        if (j->surv_dev) {
+            cudaFree(j->surv_dev);
+            j->surv_dev = nullptr;
+        }
+    }
+
+    // Pick work under the lock: a job to pre-screen, or a chunk that fits the budget.
+    bool pick(Job*& job, bool& pre, uint64_t& first, uint64_t& count, uint64_t& bytes) {
+        for (Job* j : order) {
+            if (j->state != QC_PENDING || j->cancelled) continue;
+            if (!j->prescreened) {
+                if (j->prescreening) continue;
+                j->prescreening = true;
+                job = j; pre = true;
+                return true;
+            }
+            if (j->next >= j->survivors) continue;
+            const uint64_t avail = j->survivors - j->next;
+            uint64_t n = std::min<uint64_t>(avail, CHUNK_SHOTS);
+            uint64_t slots = std::min<uint64_t>(n, (uint64_t)max_slots);
+            const uint64_t free_b = cfg.hbm_budget_bytes > inflight_bytes ? cfg.hbm_budget_bytes - inflight_bytes : 0;
+            const uint64_t fit = j->footprint ? free_b / j->footprint : slots;
+            if (fit == 0) continue;  // wait until memory frees up
+            slots = std::min(slots, fit);
+            job = j; pre = false;
+            first = j->next;
+            count = n;
+            bytes = slots * j->footprint;
+            j->next += n;
+            j->inflight += 1;
+            inflight_bytes += bytes;
+            if (j->start_ms < 0) j->start_ms = now_ms();
+            return true;
+        }
+        return false;
+    }
+
+    void worker() {
+        cudaSetDevice(device);
+        cudaStream_t s;
+        cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+        unsigned long long* counts = nullptr;
+        cudaMalloc(&counts, 3 * WBINS * sizeof(unsigned long long));
+        for (;;) {
+            Job* j = nullptr;
+            bool pre = false;
+            uint64_t first = 0, count = 0, bytes = 0;
+            {
+                std::unique_lock<std::mutex> lk(mu);
+                cv.wait(lk, [&] { return stop || pick(j, pre, first, count, bytes); });
+                if (stop && !j) break;
+            }
+            if (pre) {
+                // whole-job pre-screen; n_w counts every drawn shot (Eq. estimators)
+                uint64_t nwords = (j->nshots + 63) / 64;
+                uint64_t* mask = nullptr;
+                uint64_t* surv = nullptr;
+                qc_status st = QC_OK;
+                if (cudaMalloc(&mask, std::max<uint64_t>(nwords, 1) * 8) != cudaSuccess ||
+                    cudaMalloc(&surv, std::max<uint64_t>(j->nshots, 1) * 8) != cudaSuccess)
+                    st = fail(QC_ENOMEM, "job buffers");
+                qc_survivors sv{surv, j->nshots, 0};
+                uint64_t hd[WBINS] = {}, hk[WBINS] = {};
+                if (st == QC_OK)
+                    st = prescreen_run(*j->circ, j->noise, j->shot0, j->nshots, mask, &sv, hd, hk, WBINS - 1, s);
+                uint64_t fp = 0;
+                if (st == QC_OK) st = shot_footprint(*j->circ, j->prm, &fp);
+                cudaFree(mask);
+                std::lock_guard<std::mutex> lk(mu);
+                j->prescreening = false;
+                if (st != QC_OK) {
+                    cudaFree(surv);
+                    finish(j, st);
+                } else {
+                    j->prescreened = true;
+                    j->surv_dev = surv;
+                    j->survivors = sv.count;
+                    j->footprint = fp;
+                    for (int w = 0; w < WBINS; ++w) j->counts[w].n = hd[w];
+                    if (j->cancelled) finish(j, QC_ECANCELLED);
+                    else if (sv.count == 0) { if (j->start_ms < 0) j->start_ms = now_ms(); finish(j, QC_OK); }
+                }
+                cv.notify_all();
+                continue;
+            }
+            // a chunk of survivors
+            qc_status st = QC_OK;
+            unsigned long long h[3 * WBINS] = {};
+            if (cudaMemsetAsync(counts, 0, sizeof h, s) != cudaSuccess) st = fail(QC_EDEVICE, "memset");
+            const int slots = (int)std::max<uint64_t>(1, bytes / std::max<uint64_t>(1, j->footprint));
+            if (st == QC_OK)
+                st = engine_launch(*j->circ, j->noise, j->surv_dev + first, count, j->prm, counts, WBINS - 1, nullptr, s,
+                                   slots);
+            if (st == QC_OK && (cudaMemcpyAsync(h, counts, sizeof h, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                                cudaStreamSynchronize(s) != cudaSuccess))
+                st = fail(QC_EDEVICE, "engine chunk");
+            std::lock_guard<std::mutex> lk(mu);
+            inflight_bytes -= bytes;
+            j->inflight -= 1;
+            j->done += count;
+            for (int w = 0; w < WBINS; ++w) {
+                j->counts[w].n_acc += h[3 * w + 1];
+                j->counts[w].n_err += h[3 * w + 2];
+            }
+            if (j->state == QC_PENDING) {
+                if (st != QC_OK) finish(j, st);
+                else if (j->cancelled && j->inflight == 0) finish(j, QC_ECANCELLED);
+                else if (j->done == j->survivors && j->inflight == 0) finish(j, QC_OK);
+            }
+            cv.notify_all();
+        }
+        cudaFree(counts);
+        cudaStreamDestroy(s);
+    }
+};
+
+}  // namespace qc
+
+struct qc_server {
+    qc::Server srv;
+};
+
+using namespace qc;
+
+extern "C" qc_status mps_serve_create(const qc_serve_cfg* cfg, qc_server** out) {
+    if (!cfg || !out) return fail(QC_EINVAL, "null argument");
+    *out = nullptr;
+    std::unique_ptr<qc_server> sp(new qc_server());
+    Server& s = sp->srv;
+    s.cfg = *cfg;
+    QC_CUDA(cudaGetDevice(&s.device));
+    int nsm = 0;
+    QC_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, s.device));
+    s.max_slots = cfg->max_slots > 0 ? cfg->max_slots : nsm;
+    const int ns = cfg->n_streams > 0 ? cfg->n_streams : 2;
+    for (int i = 0; i < ns; ++i) s.workers.emplace_back([&s] { s.worker(); });
+    *out = sp.release();
+    return QC_OK;
+}
+
+extern "C" qc_status mps_serve_submit(qc_server* server, const qc_circuit* circuit, qc_noise noise,
+                                      qc_mps_params params, uint64_t shot0, uint64_t nshots, uint64_t* job_id) {
+    if (!server || !circuit || !job_id) return fail(QC_EINVAL, "null argument");
+    if (shot0 % 64) return fail(QC_EINVAL, "shot0 must be a multiple of 64");
+    if (noise.fault_weight >= 0) return fail(QC_EINVAL, "the serving loop takes Bernoulli noise");
+    if (params.chi_max < 1 || !(params.cutoff >= 0) || !(noise.p >= 0 && noise.p < 1))
+        return fail(QC_EINVAL, "bad parameters");
+    Server& s = server->srv;
+    Job* j = new Job();
+    j->circ = &const_cast<qc_circuit*>(circuit)->impl;
+    j->noise = noise;
+    j->prm = params;
+    j->shot0 = shot0;
+    j->nshots = nshots;
+    {
+        std::lock_guard<std::mutex> lk(s.mu);
+        j->id = s.next_id++;
+        j->submit_ms = s.now_ms();
+        s.jobs[j->id] = j;
+        s.order.push_back(j);
+    }
+    s.cv.notify_all();
+    *job_id = j->id;
+    return QC_OK;
+}
+
+extern "C" qc_status mps_serve_poll(qc_server* server, uint64_t job_id, qc_job_result* out) {
+    if (!server || !out) return fail(QC_EINVAL, "null argument");
+    Server& s = server->srv;
+    std::lock_guard<std::mutex> lk(s.mu);
+    auto it = s.jobs.find(job_id);
+    if (it == s.jobs.end()) return fail(QC_EINVAL, "unknown job %llu", (unsigned long long)job_id);
+    Job* j = it->second;
+    if (j->state == QC_PENDING) return QC_PENDING;
+    out->state = j->state;
+    out->shots = j->nshots;
+    out->survivors = j->survivors;
+    for (int w = 0; w < WBINS; ++w) out->counts[w] = j->counts[w];
+    out->submit_ms = j->submit_ms;
+    out->start_ms = j->start_ms;
+    out->end_ms = j->end_ms;
+    return QC_OK;
+}
+
+extern "C" qc_status mps_serve_cancel(qc_server* server, uint64_t job_id) {
+    if (!server) return fail(QC_EINVAL, "null argument");
+    Server& s = server->srv;
+    std::lock_guard<std::mutex> lk(s.mu);
+    auto it = s.jobs.find(job_id);
+    if (it == s.jobs.end()) return fail(QC_EINVAL, "unknown job");
+    Job* j = it->second;
+    if (j->state != QC_PENDING) return QC_OK;
+    j->cancelled = true;
+    if (j->inflight == 0 && !j->prescreening) s.finish(j, QC_ECANCELLED);
+    s.cv.notify_all();
+    return QC_OK;
+}
+
+extern "C" void mps_serve_destroy(qc_server* server) {
+    if (!server) return;
+    Server& s = server->srv;
+    {
+        std::lock_guard<std::mutex> lk(s.mu);
+        s.stop = true;
+        for (Job* j : s.order)
+            if (j->state == QC_PENDING) j->cancelled = true;
+    }
+    s.cv.notify_all();
+    for (auto& t : s.workers) t.join();
+    for (auto& kv : s.jobs) {
+        if (kv.second->surv_dev) cudaFree(kv.second->surv_dev);
+        delete kv.second;
+    }
+    delete server;
+}

@@ -1,0 +1,158 @@
+"""The batched MPS engine on the GPU against the FP64 oracle.
+
+Tolerances: the complex128 path agrees with the oracle's FP64 state to 1e-10 in every readout
+probability and in the fidelity; the complex64 path to 1e-4 absolute in the fidelity (readout
+decisions then agree except where a uniform draw falls within 1e-4 of p1, which the test counts).
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import mps as omps
+from oracle import prescreen, sampler
+from oracle import statevector as osv
+from oracle.circuit import parse
+from synth import random_circuit, workload_circuit
+
+from gpu_common import dev_shots, lib_ready
+
+pytestmark = pytest.mark.gpu
+
+
+def _oracle_results(text, shots, *, p, seed, engine, chi_max=1 << 30, cutoff=0.0, weight=-1):
+    oc = parse(text)
+    faults = sampler.draw_faults(oc, p=p, seed=seed, shots=shots, fault_weight=weight)
+    if engine == "sv":
+        _, ref, _ = osv.run_shot(oc, reference=True)
+    else:
+        _, ref, _ = omps.run_shot(oc, reference=True, chi_max=chi_max, cutoff=cutoff)
+    out = {}
+    for s in shots:
+        if engine == "sv":
+            st, psi, abort = osv.run_shot(oc, faults[s], seed=seed, shot=s)
+            f = osv.fidelity(ref, psi) if st == "accepted" else None
+        else:
+            st, psi, abort = omps.run_shot(oc, faults[s], seed=seed, shot=s, chi_max=chi_max, cutoff=cutoff)
+            f = omps.fidelity(ref, psi) if st == "accepted" else None
+        out[s] = (st, abort, f, len(faults[s]))
+    return out
+
+
+def _survivors(q, c, p, seed, n):
+    out = q.pauli_prescreen(c, 0, n, p=p, seed=seed)
+    return out["survivors"].cpu().numpy()
+
+
+def _compare(res, ref, ftol, allow_flip=0):
+    flips = 0
+    for r in res:
+        st, abort, f, w = ref[int(r["shot"])]
+        assert r["weight"] == w
+        assert r["status"] in (0, 1), r
+        if (r["status"] == 0) != (st == "accepted"):
+            flips += 1
+            continue
+        if st == "accepted":
+            assert abs(r["fidelity"] - f) < ftol, (r, f)
+        else:
+            assert r["abort_op"] == abort
+    assert flips <= allow_flip, flips
+    return flips
+
+
+def test_c128_d3_workload_matches_oracle():
+    """17-qubit d=3-shaped circuit, chi_max 32, cutoff 1e-12, complex128 (exact here)."""
+    q = lib_ready()
+    text = workload_circuit("d3_17q_12l")
+    c = q.Circuit(text)
+    p, seed = 4e-3, 11
+    shots = _survivors(q, c, p, seed, 64 * 6)[:40]
+    counts, res = q.mps_sample_batch(c, dev_shots(shots), p=p, seed=seed, chi_max=32, cutoff=1e-12,
+                                     precision=q.QC_C128)
+    ref = _oracle_results(text, [int(s) for s in shots], p=p, seed=seed, engine="mps", chi_max=32, cutoff=1e-12)
+    _compare(res, ref, 1e-10)
+    assert counts[:, 0].sum() == len(shots)
+    assert counts[:, 1].sum() == sum(1 for v in ref.values() if v[0] == "accepted")
+    assert (res["discarded"] < 1e-20).all()
+    assert res[res["status"] == 0]["chi_peak"].max() <= 32
+
+
+def test_c64_d3_workload_matches_oracle():
+    q = lib_ready()
+    text = workload_circuit("d3_17q_12l")
+    c = q.Circuit(text)
+    p, seed = 4e-3, 12
+    shots = _survivors(q, c, p, seed, 64 * 6)[:40]
+    _, res = q.mps_sample_batch(c, dev_shots(shots), p=p, seed=seed, chi_max=32, cutoff=1e-12, precision=q.QC_C64)
+    ref = _oracle_results(text, [int(s) for s in shots], p=p, seed=seed, engine="mps", chi_max=32, cutoff=1e-12)
+    _compare(res, ref, 1e-4, allow_flip=1)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+@pytest.mark.parametrize("prec", [1, 0])
+def test_random_circuits_match_statevector(seed, prec):
+    """Unstructured circuits: every gate, line distances up to 3 (SWAP routing), resets, faults."""
+    q = lib_ready()
+    text = random_circuit(8, 160, seed=seed, max_dist=3, p_reset=0.04)
+    c = q.Circuit(text)
+    shots = list(range(0, 48))
+    _, res = q.mps_sample_batch(c, dev_shots(shots), p=2e-2, seed=seed, chi_max=64, cutoff=0.0, precision=prec)
+    ref = _oracle_results(text, shots, p=2e-2, seed=seed, engine="sv")
+    _compare(res, ref, 1e-10 if prec == 1 else 1e-4, allow_flip=0 if prec == 1 else 1)
+
+
+def test_truncation_invariants():
+    """chi_max below the Schmidt rank: bonds capped, discarded weight reported, F <= 1."""
+    q = lib_ready()
+    text = random_circuit(10, 300, seed=3, max_dist=2, noise=False, one_q=("H", "T", "S"))
+    c = q.Circuit(text)
+    _, res = q.mps_sample_batch(c, dev_shots([0, 1]), p=0.0, seed=0, chi_max=4, cutoff=0.0, precision=q.QC_C128)
+    oc = parse(text)
+    _, exact, _ = omps.run_shot(oc, reference=True)
+    _, trunc, _ = omps.run_shot(oc, reference=True, chi_max=4)
+    for r in res:
+        assert r["status"] == 0 and r["chi_peak"] <= 4
+        assert r["discarded"] > 0
+        if r["degenerate_cuts"] == 0 and trunc.degenerate_cuts == 0:
+            assert abs(r["discarded"] - trunc.discarded) < 1e-9
+
+
+def test_exact_weight_mode():
+    q = lib_ready()
+    text = workload_circuit("d3_17q_12l", layers=5)
+    c = q.Circuit(text)
+    shots = list(range(100, 124))
+    _, res = q.mps_sample_batch(c, dev_shots(shots), p=0.0, seed=5, chi_max=32, cutoff=1e-12,
+                                precision=q.QC_C128, fault_weight=2)
+    ref = _oracle_results(text, shots, p=0.0, seed=5, engine="mps", weight=2, cutoff=1e-12)
+    assert (res["weight"] == 2).all()
+    _compare(res, ref, 1e-10)
+
+
+def test_empty_batch_and_bad_params():
+    q = lib_ready()
+    c = q.Circuit(workload_circuit("d3_17q_12l", layers=2))
+    counts, res = q.mps_sample_batch(c, dev_shots([]), p=1e-3, seed=0, chi_max=8, cutoff=0.0)
+    assert counts.sum() == 0
+    with pytest.raises(q.QcError):
+        q.mps_sample_batch(c, dev_shots([0]), p=1e-3, seed=0, chi_max=0, cutoff=0.0)
+    bad = q.Circuit("QUBITS 2\nH 0\nM 0\n")  # noiseless outcome is random: no reference state
+    with pytest.raises(q.QcError):
+        q.mps_sample_batch(bad, dev_shots([0]), p=0.0, seed=0, chi_max=4, cutoff=0.0)
+
+
+def test_d5_workload_c64_sampled_shots():
+    """49-qubit, 60-layer workload, chi_max 64, c64, in the benchmark's launch: a few survivors
+    recomputed by the FP64 oracle MPS."""
+    q = lib_ready()
+    text = workload_circuit("d5_49q_60l")
+    c = q.Circuit(text)
+    p, seed = 1e-3, 0
+    shots = _survivors(q, c, p, seed, 64 * 4096)[:32]
+    assert len(shots) >= 8
+    _, res = q.mps_sample_batch(c, dev_shots(shots), p=p, seed=seed, chi_max=64, cutoff=1e-10, precision=q.QC_C64)
+    pick = [int(s) for s in shots[:4]]
+    ref = _oracle_results(text, pick, p=p, seed=seed, engine="mps", chi_max=64, cutoff=1e-10)
+    sub = res[np.isin(res["shot"], pick)]
+    _compare(sub, ref, 1e-4, allow_flip=1)
+    assert (res["status"] >= 0).all()
