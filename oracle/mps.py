@@ -25,6 +25,7 @@ import numpy as np
 
 from . import gates
 from .philox import readout_uniform
+from .statevector import REF_RESET_THRESHOLD
 
 
 class MPS:
@@ -188,7 +189,7 @@ def run_shot(circ, faults=(), *, seed=0, shot=0, chi_max=1 << 30, cutoff=0.0, re
                         raise ValueError(f"measurement at op {idx} is not deterministic in the noiseless circuit")
                     outcome = 0
                 else:
-                    outcome = 1 if p1 > 0.5 else 0
+                    outcome = 1 if p1 > REF_RESET_THRESHOLD else 0
             else:
                 u = readout_uniform(seed, circ.readout_of_op[idx], shot)
                 outcome = 1 if u < p1 else 0

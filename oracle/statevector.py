@@ -16,6 +16,13 @@ from .philox import readout_uniform
 
 MAX_QUBITS = 26
 
+# Reference run: a reset of a qubit that is not in a definite state takes outcome 1 only when
+# p1 exceeds this value.  The paper's reference is the noiseless final state (App. A.3); its
+# resets follow post-selected measurements and are deterministic.  For other circuits a fixed
+# convention is needed, and a threshold away from the values Clifford+T amplitudes produce
+# (1/2, cos^2(pi/8), ...) keeps the choice immune to rounding.
+REF_RESET_THRESHOLD = 0.6180339887498949
+
 
 class StateVector:
     def __init__(self, n: int):
@@ -67,8 +74,8 @@ def run_shot(circ, faults=(), *, seed=0, shot=0, reference=False, record=None):
     """Run one shot.  faults: sorted (channel, code) pairs.  Returns (status, state, probs).
 
     status is 'rejected' at the first measurement returning 1, else 'accepted'.  With
-    reference=True no faults are applied, every measurement is projected on 0 and every reset
-    takes its more likely outcome; a measurement with p1 > 1e-10 then raises (the noiseless
+    reference=True no faults are applied, every measurement is projected on 0 and a reset takes
+    outcome 1 only when p1 > REF_RESET_THRESHOLD; a measurement with p1 > 1e-10 then raises (the noiseless
     circuit must return 0 deterministically for the overlap test to be defined).
     record: optional list receiving (op index, p1) for every readout."""
     sv = StateVector(circ.n)
@@ -92,7 +99,7 @@ def run_shot(circ, faults=(), *, seed=0, shot=0, reference=False, record=None):
                         raise ValueError(f"measurement at op {idx} is not deterministic in the noiseless circuit")
                     outcome = 0
                 else:
-                    outcome = 1 if p1 > 0.5 else 0
+                    outcome = 1 if p1 > REF_RESET_THRESHOLD else 0
             else:
                 u = readout_uniform(seed, circ.readout_of_op[idx], shot)
                 outcome = 1 if u < p1 else 0

@@ -171,7 +171,10 @@ struct Engine {
     }
 
     // ---- one-sided Jacobi on the columns of X (rows x cols, leading dimension ld) ---------------
-    __device__ bool jacobi(V* X, int rows, int cols, int ld) {
+    // Pairs whose smaller column is below the numerical floor are left alone: such a column is
+    // rounding noise of a rank-deficient theta, and rotating it against a large column never
+    // reaches relative orthogonality.
+    __device__ bool jacobi(V* X, int rows, int cols, int ld, R floor2) {
         const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
         constexpr int NW = NT / 32;
         const R eps = sizeof(R) == 4 ? (R)FLT_EPSILON : (R)DBL_EPSILON;
@@ -196,7 +199,7 @@ struct Engine {
                     }
                     al = warp_sum(al); be = warp_sum(be); gr = warp_sum(gr); gi = warp_sum(gi);
                     const R g = sqrt(gr * gr + gi * gi);
-                    if (g > tol * sqrt(al * be) && g > (R)0) {
+                    if (g > tol * sqrt(al * be) && g > (R)0 && fmin(al, be) > floor2) {
                         rotated = 1;
                         const R zeta = (be - al) / (2 * g);
                         const R t = (zeta >= 0 ? (R)1 : (R)-1) / (fabs(zeta) + sqrt((R)1 + zeta * zeta));
@@ -228,6 +231,7 @@ struct Engine {
         const V* A = site(q);
         const V* B = site(q + 1);
         // theta'[(l,s),(t,r)] = sum_{s',t'} g[(s,t),(s',t')] sum_k A[l,s',k] B[k,t',r]
+        double fro = 0;
         for (int e = threadIdx.x; e < cl * cr; e += NT) {
             const int l = e / cr, r = e - l * cr;
             V th[4];
@@ -249,13 +253,17 @@ struct Engine {
 #pragma unroll
                 for (int u = 0; u < 4; ++u) v = cfma(g[st * 4 + u], th[u], v);
                 const int i = l * 2 + (st >> 1), j = (st & 1) * cr + r;
+                fro += (double)v.x * v.x + (double)v.y * v.y;
                 tcopy[(size_t)i * n + j] = v;
                 if (right) X[(size_t)j * ld + i] = v;
                 else X[(size_t)i * ld + j] = cmk<V>(v.x, -v.y);
             }
         }
-        __syncthreads();
-        if (!jacobi(X, rows, cols, ld)) {
+        fro = block_sum<NT>(fro, S.red);
+        const R eps = sizeof(R) == 4 ? (R)FLT_EPSILON : (R)DBL_EPSILON;
+        const R fl = (R)4 * eps * sqrt((R)rows);
+        const R floor2 = fl * fl * (R)fro;
+        if (!jacobi(X, rows, cols, ld, floor2)) {
             status = QC_ENOCONV;
             return;
         }
@@ -282,7 +290,11 @@ struct Engine {
         // truncation rule, FP64: smallest r >= 1 with discarded tail <= cutoff * total, r <= chi_max
         if (threadIdx.x == 0) {
             double tot = 0;
-            for (int k = 0; k < cols; ++k) tot += (double)S.sig2[k];
+            int nz = 0;
+            for (int k = 0; k < cols; ++k) {
+                tot += (double)S.sig2[k];
+                nz += S.sig2[k] > floor2;
+            }
             const double thr = P.cutoff * tot;
             int r = cols;
             double tail = 0;
@@ -290,7 +302,7 @@ struct Engine {
                 tail += (double)S.sig2[S.perm[r - 1]];
                 --r;
             }
-            while (r > P.chi_max) {
+            while (r > P.chi_max || (r > 1 && r > nz)) {
                 tail += (double)S.sig2[S.perm[r - 1]];
                 --r;
             }
@@ -387,7 +399,8 @@ struct Engine {
                 }
                 outcome = 0;
             } else {
-                outcome = pr1 > 0.5 ? 1 : 0;
+                // a reset of an undetermined qubit: fixed convention, robust to rounding at p1 = 1/2
+                outcome = pr1 > 0.6180339887498949 ? 1 : 0;
             }
         } else {
             const double u = readout_uniform(rid, shot, P.k0, P.k1);
