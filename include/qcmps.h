@@ -151,6 +151,10 @@ typedef struct {
     double discarded;        /* summed discarded weight of all truncations (FP64) */
     int32_t degenerate_cuts; /* truncations whose last kept and first dropped values tie */
     int32_t n_updates;       /* two-site updates performed */
+    double alg_flops;        /* algorithmic real flops of the shot's two-site updates: contraction
+                                8(2chi_l)chi_m(2chi_r), gate 128 chi_l chi_r, split by the R-SVD count
+                                4(4 M^2 N + 22 N^3) (M >= N the sides of theta) plus the projection
+                                8 r M N */
 } qc_shot_result;
 
 /* Simulate the given shots (typically pre-screen survivors) as MPS: single-site gates in place;

@@ -14,7 +14,7 @@ from . import _native as N
 
 SHOT_DTYPE = np.dtype([("shot", "<u8"), ("status", "<i4"), ("weight", "<i4"), ("logical_error", "<i4"),
                        ("chi_peak", "<i4"), ("abort_op", "<i8"), ("fidelity", "<f8"), ("discarded", "<f8"),
-                       ("degenerate_cuts", "<i4"), ("n_updates", "<i4")])
+                       ("degenerate_cuts", "<i4"), ("n_updates", "<i4"), ("alg_flops", "<f8")])
 assert SHOT_DTYPE.itemsize == C.sizeof(N.ShotResult)
 
 
@@ -111,21 +111,24 @@ def pauli_prescreen(circ: Circuit, shot0: int, nshots: int, *, p: float, seed: i
 
 def mps_sample_batch(circ: Circuit, shots: torch.Tensor, *, p: float, seed: int, chi_max: int, cutoff: float,
                      precision: int = N.QC_C64, tau: float = 0.0, w_max: int = 15, fault_weight: int = -1,
-                     per_shot: bool = True, per_shot_buf: torch.Tensor | None = None, stream=None):
-    """Returns (counts[w_max+1, 3] numpy uint64 (n, n_acc, n_err), per-shot structured array or None)."""
+                     per_shot: bool = True, per_shot_buf: torch.Tensor | None = None, copy_back: bool = True,
+                     stream=None):
+    """Returns (counts[w_max+1, 3] numpy uint64 (n, n_acc, n_err), per-shot structured array or None).
+
+    With copy_back=False the per-shot results stay in per_shot_buf on the device."""
     shots = _dev_u64(shots)
     n = shots.numel()
     counts = (N.Counts * (w_max + 1))()
     buf = None
     if per_shot:
-        buf = per_shot_buf if per_shot_buf is not None else torch.empty(
+        buf = per_shot_buf if per_shot_buf is not None else torch.zeros(
             max(n, 1) * SHOT_DTYPE.itemsize, dtype=torch.uint8, device=shots.device)
     prm = N.MpsParams(chi_max, cutoff, precision, tau)
     N.check(N.lib().mps_sample_batch(circ.handle, N.Noise(p, seed, fault_weight), _ptr(shots), n, prm,
                                      C.cast(counts, C.c_void_p), w_max, _ptr(buf), _stream(stream)))
     arr = np.array([[c.n, c.n_acc, c.n_err] for c in counts], dtype=np.uint64)
     res = None
-    if per_shot:
+    if per_shot and copy_back:
         res = np.frombuffer(buf[: n * SHOT_DTYPE.itemsize].cpu().numpy().tobytes(), dtype=SHOT_DTYPE)
     return arr, res
 
@@ -167,3 +170,8 @@ class Server:
 
     def __del__(self):
         self.close()
+
+
+def shot_results(buf: torch.Tensor, n: int) -> np.ndarray:
+    """Per-shot results left on the device by mps_sample_batch(copy_back=False)."""
+    return np.frombuffer(buf[: n * SHOT_DTYPE.itemsize].cpu().numpy().tobytes(), dtype=SHOT_DTYPE)

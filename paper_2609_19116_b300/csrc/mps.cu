@@ -137,6 +137,7 @@ struct Engine {
     int chi_peak;
     int nupd;
     int64_t abort_op;
+    double flops;
 
     __device__ Engine(const EngineParams<R>& p, Shared<R>& s, int slot_id)
         : P(p), S(s) {
@@ -372,6 +373,11 @@ struct Engine {
         __syncthreads();
         chi_peak = max(chi_peak, r);
         ++nupd;
+        {
+            const double M = (double)max(m, n), Nn = (double)min(m, n);
+            flops += 8.0 * m * cm * n + 128.0 * cl * cr + 4.0 * (4.0 * M * M * Nn + 22.0 * Nn * Nn * Nn) +
+                     8.0 * r * m * n;
+        }
     }
 
     // ---- readout on site q (the orthogonality centre) ------------------------------------------
@@ -544,7 +550,7 @@ struct Engine {
 
     __device__ void run(uint64_t task) {
         const uint64_t shot = P.reference ? 0 : P.shots[task];
-        status = 0; disc = 0; degen = 0; chi_peak = 1; nupd = 0; abort_op = -1;
+        status = 0; disc = 0; degen = 0; chi_peak = 1; nupd = 0; abort_op = -1; flops = 0;
         for (int q = threadIdx.x; q <= P.nq; q += NT) S.dims[q] = 1;
         for (int q = threadIdx.x; q < P.nq; q += NT) {
             V* a = site(q);
@@ -626,6 +632,7 @@ struct Engine {
                     res.discarded = disc;
                     res.degenerate_cuts = degen;
                     res.n_updates = nupd;
+                    res.alg_flops = flops;
                     P.per_shot[task] = res;
                 }
             }
