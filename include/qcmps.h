@@ -125,6 +125,29 @@ qc_status pauli_prescreen(const qc_circuit* circuit, qc_noise noise, uint64_t sh
                           uint64_t nshots, uint64_t* kept_mask_dev, qc_survivors* survivors,
                           uint64_t* hist_drawn, uint64_t* hist_kept, int32_t w_max, void* stream);
 
+/* The same pre-screen for callers that cannot allocate device memory: code inside an allocation-
+ * free region (a stream capture they do not own, a process whose device memory is a fixed pool
+ * owned by someone else, an embedding runtime that forbids cudaMalloc).  The paper has no
+ * counterpart; it is a deployment convenience.  This entry point calls no cudaMalloc, cudaFree or
+ * other allocating routine: its scratch (the staged frame program, the per-weight histograms and
+ * the compaction offsets) lives in one file-scope device array of about 1.1 MB that every GPU
+ * loading the library holds until the process exits.
+ *   limits   at most 131072 frame-program words per circuit and 536,870,912 shots per call;
+ *            larger requests return QC_ECAPACITY
+ *   outputs  as pauli_prescreen: kept_mask_dev (ceil(nshots/64) words), survivors_dev (capacity
+ *            shot indices, increasing), *n_kept (host; may exceed capacity), hist_drawn/hist_kept
+ *            (optional host arrays of w_max+1 counts)
+ *   set-up   the first call on a device looks up the array's device address
+ *            (cudaGetSymbolAddress) with that device current; make that first call before any
+ *            stream capture
+ *   sharing  every call uses the same array and clears what must start at zero; calls whose work
+ *            overlaps on the GPU (two streams, two host threads) race on it and must be serialised
+ *            by the caller.  Synchronises `stream` before returning. */
+qc_status pauli_prescreen_noalloc(const qc_circuit* circuit, qc_noise noise, uint64_t shot0,
+                                  uint64_t nshots, uint64_t* kept_mask_dev, uint64_t* survivors_dev,
+                                  uint64_t capacity, uint64_t* n_kept, uint64_t* hist_drawn,
+                                  uint64_t* hist_kept, int32_t w_max, void* stream);
+
 /* ---- batched MPS sampling (Sec. 3.1, 4, 4.3) --------------------------------------------- */
 
 enum { QC_C64 = 0, QC_C128 = 1 };

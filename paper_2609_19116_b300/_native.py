@@ -80,6 +80,8 @@ def lib():
             "qc_circuit_decided": (C.c_int, [vp, vp]),
             "qc_sample_faults": (C.c_int, [vp, Noise, vp, u64, C.c_uint32, vp, vp, vp, vp]),
             "pauli_prescreen": (C.c_int, [vp, Noise, u64, u64, vp, C.POINTER(Survivors), vp, vp, i32, vp]),
+            "pauli_prescreen_noalloc": (C.c_int, [vp, Noise, u64, u64, vp, vp, u64, C.POINTER(u64), vp, vp, i32,
+                                                  vp]),
             "mps_sample_batch": (C.c_int, [vp, Noise, vp, u64, MpsParams, vp, i32, vp, vp]),
             "mps_shot_footprint": (C.c_int, [vp, MpsParams, C.POINTER(u64)]),
             "mps_serve_create": (C.c_int, [C.POINTER(ServeCfg), C.POINTER(vp)]),
@@ -103,5 +105,5 @@ def check(status: int):
 
 
 EXPORTED = ("qc_last_error", "qc_circuit_parse", "qc_circuit_free", "qc_circuit_get_info", "qc_circuit_decided",
-            "qc_sample_faults", "pauli_prescreen", "mps_sample_batch", "mps_shot_footprint", "mps_serve_create",
+            "qc_sample_faults", "pauli_prescreen", "pauli_prescreen_noalloc", "mps_sample_batch", "mps_shot_footprint", "mps_serve_create",
             "mps_serve_submit", "mps_serve_poll", "mps_serve_cancel", "mps_serve_destroy")

@@ -466,3 +466,122 @@ extern "C" qc_status pauli_prescreen(const qc_circuit* circuit, qc_noise noise, 
     return prescreen_run(const_cast<qc_circuit*>(circuit)->impl, noise, shot0, nshots, kept_mask_dev, survivors,
                          hist_drawn, hist_kept, w_max, (cudaStream_t)stream);
 }
+
+// ---- pre-screen variant for callers that cannot allocate device memory ------------------------
+// Some callers cannot call cudaMalloc at all: code running inside a region that forbids
+// allocation (a CUDA-graph capture they do not control, a memory-pool-locked serving process with
+// a fixed device-memory budget, an embedding runtime that owns every allocation).  This variant
+// keeps all of its scratch -- the staged frame program, the per-weight histograms and the
+// compaction offsets -- in one file-scope device array instead of allocating it.  The array is
+// part of the library image: every GPU that loads the library holds it until the process exits.
+namespace qc {
+namespace {
+
+constexpr uint64_t NA_MAX_PROG = 131072;   // frame-program words (8 bytes each)
+constexpr uint64_t NA_MAX_CHUNKS = 8192;   // compaction chunks of 1024 words: 536,870,912 shots
+constexpr uint64_t NA_BYTES = NA_MAX_PROG * sizeof(PreOp) + (2 * WMAX_BINS + NA_MAX_CHUNKS + 8) * sizeof(uint64_t);
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_BYTES];
+
+std::mutex g_na_mu;
+std::map<int, unsigned char*> g_na_addr;  // device -> address of g_noalloc_scratch on that device
+
+// The host-side name g_noalloc_scratch is a stand-in, not a device address: take the address on
+// the current device once and pass that to the kernels.
+qc_status noalloc_scratch(unsigned char** out) {
+    int d = 0;
+    QC_CUDA(cudaGetDevice(&d));
+    std::lock_guard<std::mutex> lk(g_na_mu);
+    auto it = g_na_addr.find(d);
+    if (it == g_na_addr.end()) {
+        unsigned char* ptr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress((void**)&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+        it = g_na_addr.emplace(d, ptr).first;
+    }
+    *out = it->second;
+    return QC_OK;
+}
+
+}  // namespace
+}  // namespace qc
+
+extern "C" qc_status pauli_prescreen_noalloc(const qc_circuit* circuit, qc_noise noise, uint64_t shot0,
+                                             uint64_t nshots, uint64_t* kept_mask_dev, uint64_t* survivors_dev,
+                                             uint64_t capacity, uint64_t* n_kept, uint64_t* hist_drawn,
+                                             uint64_t* hist_kept, int32_t w_max, void* stream) {
+    using namespace qc;
+    if (!circuit || !n_kept) return fail(QC_EINVAL, "null argument");
+    const CircuitImpl& c = circuit->impl;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!(noise.p >= 0.0 && noise.p < 1.0)) return fail(QC_EINVAL, "p must lie in [0, 1)");
+    if (noise.fault_weight >= 0) return fail(QC_EINVAL, "the pre-screen takes Bernoulli noise (fault_weight = -1)");
+    if (shot0 % 64) return fail(QC_EINVAL, "shot0 must be a multiple of 64");
+    if ((shot0 + nshots) / 64 >= (1ull << 32)) return fail(QC_EINVAL, "shot index beyond the 2^38 range of the contract");
+    if (w_max < 0 || w_max >= WMAX_BINS) return fail(QC_EINVAL, "w_max must lie in [0, 63]");
+    if (nshots && !kept_mask_dev) return fail(QC_EINVAL, "null kept mask");
+    if (capacity && !survivors_dev) return fail(QC_EINVAL, "null survivor buffer");
+    const uint64_t nwords = (nshots + 63) / 64;
+    const uint64_t nchunks = (nwords + CMP_CHUNK - 1) / CMP_CHUNK;
+    if (c.pre.size() > NA_MAX_PROG)
+        return fail(QC_ECAPACITY, "circuit needs %zu frame-program words; this entry point holds at most %llu",
+                    c.pre.size(), (unsigned long long)NA_MAX_PROG);
+    if (nchunks > NA_MAX_CHUNKS)
+        return fail(QC_ECAPACITY, "%llu shots exceed the %llu this entry point handles per call",
+                    (unsigned long long)nshots, (unsigned long long)(NA_MAX_CHUNKS * CMP_CHUNK * 64));
+    const size_t smem = 2ull * c.n * PRE_THREADS * sizeof(uint64_t) + PRE_CHUNK * sizeof(PreOp) +
+                        64 * sizeof(uint32_t) + 2 * WMAX_BINS * sizeof(unsigned long long);
+    if (smem > 227 * 1024) return fail(QC_EINVAL, "too many qubits for the pre-screen frame (%d)", c.n);
+    unsigned char* base = nullptr;
+    qc_status st = noalloc_scratch(&base);
+    if (st != QC_OK) return st;
+    if (nshots == 0) {
+        *n_kept = 0;
+        for (int i = 0; hist_drawn && i <= w_max; ++i) hist_drawn[i] = 0;
+        for (int i = 0; hist_kept && i <= w_max; ++i) hist_kept[i] = 0;
+        return QC_OK;
+    }
+    PreOp* prog = reinterpret_cast<PreOp*>(base);
+    uint64_t* hist = reinterpret_cast<uint64_t*>(base + NA_MAX_PROG * sizeof(PreOp));  // [2 * WMAX_BINS]
+    uint64_t* chunk = hist + 2 * WMAX_BINS;                                             // [nchunks]
+    uint64_t* total = chunk + NA_MAX_CHUNKS;                                            // [1]
+    // the array keeps the previous call's contents: stage the program, clear the counters
+    if (!c.pre.empty())
+        QC_CUDA(cudaMemcpyAsync(prog, c.pre.data(), c.pre.size() * sizeof(PreOp), cudaMemcpyHostToDevice, s));
+    QC_CUDA(cudaMemsetAsync(hist, 0, 2 * WMAX_BINS * sizeof(uint64_t), s));
+    QC_CUDA(cudaMemsetAsync(total, 0, sizeof(uint64_t), s));
+    PreParams P{};
+    P.prog = prog;
+    P.nops = (uint32_t)c.pre.size();
+    P.nq = (uint32_t)c.n;
+    P.nchan = (uint32_t)c.chan_kind.size();
+    P.chan_kind = nullptr;  // the frame program carries the channel kinds
+    P.word0 = shot0 / 64;
+    P.nwords = nwords;
+    P.nshots = nshots;
+    P.k0 = (uint32_t)noise.seed;
+    P.k1 = (uint32_t)(noise.seed >> 32);
+    const Thresholds th = make_thresholds(noise.p);
+    for (int i = 0; i < 64; ++i) P.tg[i] = th.tg[i];
+    P.wmax = w_max;
+    P.kept = kept_mask_dev;
+    P.hist_drawn = reinterpret_cast<unsigned long long*>(hist);
+    P.hist_kept = P.hist_drawn + WMAX_BINS;
+    QC_CUDA(cudaFuncSetAttribute(prescreen_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    prescreen_kernel<<<(unsigned)((nwords + PRE_THREADS - 1) / PRE_THREADS), PRE_THREADS, smem, s>>>(P);
+    QC_CUDA(cudaGetLastError());
+    compact_count<<<(unsigned)nchunks, CMP_THREADS, 0, s>>>(kept_mask_dev, nwords, chunk);
+    compact_scan<<<1, 1024, 0, s>>>(chunk, nchunks, total);
+    compact_write<<<(unsigned)nchunks, CMP_THREADS, 0, s>>>(kept_mask_dev, nwords, chunk, shot0, survivors_dev,
+                                                           capacity);
+    QC_CUDA(cudaGetLastError());
+    uint64_t h[2 * WMAX_BINS];
+    uint64_t cnt = 0;
+    QC_CUDA(cudaMemcpyAsync(h, hist, sizeof h, cudaMemcpyDeviceToHost, s));
+    QC_CUDA(cudaMemcpyAsync(&cnt, total, sizeof cnt, cudaMemcpyDeviceToHost, s));
+    QC_CUDA(cudaStreamSynchronize(s));
+    *n_kept = cnt;
+    for (int i = 0; hist_drawn && i <= w_max; ++i) hist_drawn[i] = h[i];
+    for (int i = 0; hist_kept && i <= w_max; ++i) hist_kept[i] = h[WMAX_BINS + i];
+    return QC_OK;
+}
