@@ -174,6 +174,7 @@ typedef struct {
     double discarded;        /* summed discarded weight of all truncations (FP64) */
     int32_t degenerate_cuts; /* truncations whose last kept and first dropped values tie */
     int32_t n_updates;       /* two-site updates performed */
+    int32_t sweeps;          /* Jacobi sweeps summed over the shot's two-site updates */
     double alg_flops;        /* algorithmic real flops of the shot's two-site updates: contraction
                                 8(2chi_l)chi_m(2chi_r), gate 128 chi_l chi_r, split by the R-SVD count
                                 4(4 M^2 N + 22 N^3) (M >= N the sides of theta) plus the projection

@@ -48,7 +48,7 @@ class ShotResult(C.Structure):
     _fields_ = [("shot", C.c_uint64), ("status", C.c_int32), ("weight", C.c_int32),
                 ("logical_error", C.c_int32), ("chi_peak", C.c_int32), ("abort_op", C.c_int64),
                 ("fidelity", C.c_double), ("discarded", C.c_double), ("degenerate_cuts", C.c_int32),
-                ("n_updates", C.c_int32), ("alg_flops", C.c_double)]
+                ("n_updates", C.c_int32), ("sweeps", C.c_int32), ("alg_flops", C.c_double)]
 
 
 class ServeCfg(C.Structure):

@@ -1,6 +1,7 @@
 // Circuit parsing, the offline stabiliser analysis (Sec. 4.2) and compilation of the device
 // programs: the Pauli-frame program of the pre-screen and the site-operation program of the MPS
 // engine (SWAP routing, Sec. 3.1, and orthogonality-centre planning).
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -189,10 +190,79 @@ static uint32_t g1_index(uint8_t k) {
     }
 }
 
+// Execution order of the instructions for the MPS engine.  Instructions on disjoint qubits
+// commute, so the order may follow the orthogonality centre instead of the text: a greedy list
+// schedule over the dependency graph (each qubit's instructions stay in text order) that always
+// takes the ready instruction closest to the current centre.  Readouts (M and R) also stay in text
+// order among themselves, so every readout sees the same earlier projections as in text order
+// and a shot's sampled outcomes do not depend on the schedule.
+static std::vector<size_t> schedule_ops(const CircuitImpl& c) {
+    const size_t N = c.ops.size();
+    std::vector<std::vector<uint32_t>> succ(N);
+    std::vector<int> indeg(N, 0);
+    std::vector<long> last_q(c.n, -1);
+    long last_read = -1;
+    for (size_t i = 0; i < N; ++i) {
+        const Op& op = c.ops[i];
+        long deps[3] = {last_q[op.q0], op.q1 >= 0 ? last_q[op.q1] : -1,
+                        (op.kind == K_M || op.kind == K_R) ? last_read : -1};
+        for (int a = 0; a < 3; ++a) {
+            if (deps[a] < 0) continue;
+            bool dup = false;
+            for (int b = 0; b < a; ++b) dup |= deps[b] == deps[a];
+            if (dup) continue;
+            succ[deps[a]].push_back((uint32_t)i);
+            ++indeg[i];
+        }
+        last_q[op.q0] = (long)i;
+        if (op.q1 >= 0) last_q[op.q1] = (long)i;
+        if (op.kind == K_M || op.kind == K_R) last_read = (long)i;
+    }
+    std::vector<uint32_t> ready;
+    for (size_t i = 0; i < N; ++i)
+        if (indeg[i] == 0) ready.push_back((uint32_t)i);
+    std::vector<size_t> order;
+    order.reserve(N);
+    int center = 0;
+    auto needs_center = [&](const Op& op) {
+        return op.kind == K_CX || op.kind == K_CZ || op.kind == K_SWAP || op.kind == K_M || op.kind == K_R;
+    };
+    while (!ready.empty()) {
+        // instructions that need no centre go first (lowest text index), else the nearest one
+        size_t best = 0;
+        long best_key = -1;
+        for (size_t k = 0; k < ready.size(); ++k) {
+            const Op& op = c.ops[ready[k]];
+            long dist = 0;
+            if (needs_center(op)) {
+                const int lo = op.q1 >= 0 ? std::min(op.q0, op.q1) : op.q0;
+                const int hi = op.q1 >= 0 ? std::max(op.q0, op.q1) : op.q0;
+                dist = 1 + (center < lo ? lo - center : center > hi ? center - hi : 0);
+            }
+            const long key = dist * (long)(N + 1) + (long)ready[k];
+            if (best_key < 0 || key < best_key) { best_key = key; best = k; }
+        }
+        const uint32_t i = ready[best];
+        ready[best] = ready.back();
+        ready.pop_back();
+        order.push_back(i);
+        const Op& op = c.ops[i];
+        if (needs_center(op)) {
+            const int lo = op.q1 >= 0 ? std::min(op.q0, op.q1) : op.q0;
+            const int hi = op.q1 >= 0 ? std::max(op.q0, op.q1) : op.q0;
+            center = center < lo ? lo : (center > hi ? hi : center);
+        }
+        for (uint32_t sx : succ[i])
+            if (--indeg[sx] == 0) ready.push_back(sx);
+    }
+    return order;
+}
+
 static void compile_mps(CircuitImpl& c) {
-    // 1. expand into site operations with SWAP routing (Sec. 3.1).
+    // 1. expand into site operations with SWAP routing (Sec. 3.1), in the scheduled order.
     std::vector<SiteOp> s;
-    for (size_t i = 0; i < c.ops.size(); ++i) {
+    const std::vector<size_t> order = schedule_ops(c);
+    for (size_t i : order) {
         const Op& op = c.ops[i];
         const int32_t src = (int32_t)i;
         switch (op.kind) {

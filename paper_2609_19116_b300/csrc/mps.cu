@@ -15,6 +15,8 @@
 #include <cfloat>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
+#include <cstring>
 #include <vector>
 
 #include "philox.cuh"
@@ -38,8 +40,8 @@ template <typename V> __device__ __forceinline__ V cfmac(V a, V b, V c) {  // co
     return cmk<V>(fma(a.x, b.x, fma(a.y, b.y, c.x)), fma(a.x, b.y, fma(-a.y, b.x, c.y)));
 }
 
-constexpr int MAXF = 256;     // faults per shot
-constexpr int OPCH = 64;      // program ops staged per step
+constexpr int MAXF = 128;     // faults per shot
+constexpr int OPCH = 32;      // program ops staged per step
 
 template <typename R>
 struct EngineParams {
@@ -62,6 +64,7 @@ struct EngineParams {
     uint64_t scratch_stride;
     uint64_t xg_elems;    // size of the X part of a slot's scratch
     uint32_t x_smem;      // capacity (elements) of the shared-memory X
+    uint32_t x_big;       // warp mode: capacity (elements) of the CTA's shared large work area
     int chi_max;
     double cutoff;
     uint32_t k0, k1;
@@ -79,6 +82,7 @@ struct EngineParams {
     unsigned long long* counts;  // [3*(wmax+1)]
     int wmax;
     int* ref_status;      // reference run: 0 ok, else index+1 of the bad measurement
+    int* ref_chi_out;     // reference run: chi_peak
     int* ref_dims_out;    // reference run: bond dims [nq+1]
     double* ref_disc_out;
     int sweep_cap;
@@ -91,10 +95,13 @@ struct Shared {
     int* dims;    // [nq+1]
     uint32_t* fch;
     uint8_t* fcode;
-    R* sig2;      // [2*chi_cap]
-    int* perm;    // [2*chi_cap]
     double* red;  // [64]
     MpsOp* ops;   // [OPCH]
+    V* pend;      // [nq][4]: single-qubit gates (and fault Paulis) not yet applied to the site
+    V* gate;      // [16]: the 4x4 gate of the current two-site update with the pending gates fused
+    int* nf;      // fault count of the current shot
+    V* big;       // warp mode: the CTA's shared work area for updates too large for X
+    int* big_lock;
 };
 
 template <typename R>
@@ -105,15 +112,27 @@ __device__ __forceinline__ R warp_sum(R v) {
 }
 
 // Block-wide sum of a double; every thread gets the result.
+// Barriers of an engine: in warp mode (NT = 32) every warp of the CTA runs its own shot, so the
+// engine's barriers are warp barriers.
+template <int NT> __device__ __forceinline__ void bsync() {
+    if (NT == 32) __syncwarp(); else __syncthreads();
+}
+template <int NT> __device__ __forceinline__ int bsync_or(int v) {
+    if (NT == 32) return __any_sync(0xFFFFFFFFu, v);
+    return __syncthreads_or(v);
+}
+
+// Sum of a double over the engine's threads; every thread gets the result.
 template <int NT>
-__device__ double block_sum(double v, double* red) {
+__device__ double block_sum(double v, double* red, int tid) {
     v = warp_sum<double>(v);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (NT == 32) return v;
+    const int lane = tid & 31, wid = tid >> 5;
     __syncthreads();
     if (lane == 0) red[wid] = v;
     __syncthreads();
     double t = 0;
-    if (threadIdx.x < 32) {
+    if (tid < 32) {
         t = lane < NT / 32 ? red[lane] : 0.0;
         t = warp_sum<double>(t);
         if (lane == 0) red[32] = t;
@@ -121,6 +140,13 @@ __device__ double block_sum(double v, double* red) {
     __syncthreads();
     return red[32];
 }
+
+// Rotation parameters of one Jacobi pair: FP32 uses the hardware reciprocal square root and fast
+// division (the rotation only needs c^2 + s^2 = 1 to rounding), FP64 the correctly rounded forms.
+__device__ __forceinline__ float rs_sqrt(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rs_sqrt(double x) { return 1.0 / sqrt(x); }
+__device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double fdiv(double a, double b) { return a / b; }
 
 template <typename R, int NT>
 struct Engine {
@@ -130,6 +156,7 @@ struct Engine {
     V* slot;      // this CTA's site tensors
     V* xg;        // global X
     V* tcopy;     // theta copy
+    R* gsig2;     // singular values and their order when the work area is in global memory
     // per-shot state (uniform, kept in registers of every thread, updated identically)
     int status;
     double disc;
@@ -138,21 +165,53 @@ struct Engine {
     int nupd;
     int64_t abort_op;
     double flops;
+    int sweeps;
 
-    __device__ Engine(const EngineParams<R>& p, Shared<R>& s, int slot_id)
-        : P(p), S(s) {
+    const int tid_;  // thread index within the engine (the warp lane in warp mode)
+
+    __device__ Engine(const EngineParams<R>& p, Shared<R>& s, int slot_id, int tid)
+        : P(p), S(s), tid_(tid) {
         slot = P.mps + (uint64_t)slot_id * P.slot_stride;
         xg = P.scratch + (uint64_t)slot_id * P.scratch_stride;
         tcopy = xg + P.xg_elems;
+        gsig2 = reinterpret_cast<R*>(tcopy + (size_t)(2 * P.chi_max) * (2 * P.chi_max));
     }
 
     __device__ V* site(int q) { return slot + P.off[q]; }
 
-    // ---- single-site gate in place: a[l,s,r] <- sum_t g[s,t] a[l,t,r] --------------------------
-    __device__ void apply1(int q, V g00, V g01, V g10, V g11) {
+    // ---- single-qubit gates are deferred: pend[q] <- g pend[q] (thread 0 only; consumers start
+    //      with a barrier).  A gate on the physical index keeps the canonical form, so it can wait
+    //      until the next two-site update or readout of its site, where it is fused.
+    __device__ void defer1(int q, V g00, V g01, V g10, V g11) {
+        if (tid_ != 0) return;
+        V* u = S.pend + q * 4;
+        const V u00 = u[0], u01 = u[1], u10 = u[2], u11 = u[3];
+        u[0] = cfma(g00, u00, cmul(g01, u10));
+        u[1] = cfma(g00, u01, cmul(g01, u11));
+        u[2] = cfma(g10, u00, cmul(g11, u10));
+        u[3] = cfma(g10, u01, cmul(g11, u11));
+    }
+
+    __device__ void defer_pauli(int q, uint32_t p) {
+        if (p == 0) return;
+        const V z = cmk<V>(0, 0), one = cmk<V>(1, 0), mone = cmk<V>(-1, 0);
+        if (p == 1) defer1(q, z, one, one, z);
+        else if (p == 2) defer1(q, z, cmk<V>(0, -1), cmk<V>(0, 1), z);
+        else defer1(q, one, z, z, mone);
+    }
+
+    __device__ void reset_pend(int q) {
+        V* u = S.pend + q * 4;
+        u[0] = cmk<V>(1, 0); u[1] = cmk<V>(0, 0); u[2] = cmk<V>(0, 0); u[3] = cmk<V>(1, 0);
+    }
+
+    // Apply site q's pending gate to its tensor (all threads; ends with a barrier).
+    __device__ void flush_site(int q) {
+        const V* u = S.pend + q * 4;
+        const V g00 = u[0], g01 = u[1], g10 = u[2], g11 = u[3];
         const int cl = S.dims[q], cr = S.dims[q + 1];
         V* a = site(q);
-        for (int e = threadIdx.x; e < cl * cr; e += NT) {
+        for (int e = tid_; e < cl * cr; e += NT) {
             const int l = e / cr, r = e - l * cr;
             V* p0 = a + (l * 2) * cr + r;
             V* p1 = p0 + cr;
@@ -160,80 +219,153 @@ struct Engine {
             *p0 = cfma(g00, x, cmul(g01, y));
             *p1 = cfma(g10, x, cmul(g11, y));
         }
-        __syncthreads();
-    }
-
-    __device__ void apply_pauli(int q, uint32_t p) {
-        if (p == 0) return;
-        const V z = cmk<V>(0, 0), one = cmk<V>(1, 0), mone = cmk<V>(-1, 0);
-        if (p == 1) apply1(q, z, one, one, z);
-        else if (p == 2) apply1(q, z, cmk<V>(0, -1), cmk<V>(0, 1), z);
-        else apply1(q, one, z, z, mone);
+        bsync<NT>();
+        if (tid_ == 0) reset_pend(q);
+        bsync<NT>();
     }
 
     // ---- one-sided Jacobi on the columns of X (rows x cols, leading dimension ld) ---------------
+    // Round-robin ordering: n-1 rounds of n/2 disjoint column pairs.  The pairs of a round are
+    // spread over the warps, and within a warp over lane groups of g lanes (g = 32 / pairs per warp,
+    // rounded), so that small matrices keep every lane busy and reduce over short shuffle trees.
     // Pairs whose smaller column is below the numerical floor are left alone: such a column is
     // rounding noise of a rank-deficient theta, and rotating it against a large column never
     // reaches relative orthogonality.
     __device__ bool jacobi(V* X, int rows, int cols, int ld, R floor2) {
-        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        const int lane = tid_ & 31, wid = tid_ >> 5;
         constexpr int NW = NT / 32;
         const R eps = sizeof(R) == 4 ? (R)FLT_EPSILON : (R)DBL_EPSILON;
         const R tol = (R)4 * eps * sqrt((R)rows);
         const int half = cols / 2, cm1 = cols - 1;
+        const int ppw = (half + NW - 1) / NW;
+        int G = 1;
+        while (G < ppw && G < 32) G <<= 1;
+        while (G > 1 && 32 / G < 2 && rows > 32 / G) G >>= 1;  // keep at least 2 lanes per pair when useful
+        const int g = 32 / G, grp = lane / g, gl = lane - grp * g;
         for (int sweep = 0; sweep < P.sweep_cap; ++sweep) {
             int rotated = 0;
             for (int k = 0; k < cm1; ++k) {
-                for (int pr = wid; pr < half; pr += NW) {
-                    const int sa = pr, sb = cols - 1 - pr;
+                for (int base = wid * G; base < half; base += NW * G) {
+                    const int pr = base + grp;
+                    const bool act = pr < half;
+                    const int sa = act ? pr : 0, sb = cols - 1 - sa;
                     const int ca = sa == 0 ? 0 : 1 + (sa - 1 + k) % cm1;
                     const int cb = 1 + (sb - 1 + k) % cm1;
                     V* a = X + (size_t)ca * ld;
                     V* b = X + (size_t)cb * ld;
                     R al = 0, be = 0, gr = 0, gi = 0;
-                    for (int i = lane; i < rows; i += 32) {
-                        const V x = a[i], y = b[i];
-                        al = fma(x.x, x.x, fma(x.y, x.y, al));
-                        be = fma(y.x, y.x, fma(y.y, y.y, be));
-                        gr = fma(x.x, y.x, fma(x.y, y.y, gr));
-                        gi = fma(x.x, y.y, fma(-x.y, y.x, gi));
+                    if (act)
+                        for (int i = gl; i < rows; i += g) {
+                            const V x = a[i], y = b[i];
+                            al = fma(x.x, x.x, fma(x.y, x.y, al));
+                            be = fma(y.x, y.x, fma(y.y, y.y, be));
+                            gr = fma(x.x, y.x, fma(x.y, y.y, gr));
+                            gi = fma(x.x, y.y, fma(-x.y, y.x, gi));
+                        }
+                    for (int o = g >> 1; o > 0; o >>= 1) {
+                        al += __shfl_xor_sync(0xFFFFFFFFu, al, o);
+                        be += __shfl_xor_sync(0xFFFFFFFFu, be, o);
+                        gr += __shfl_xor_sync(0xFFFFFFFFu, gr, o);
+                        gi += __shfl_xor_sync(0xFFFFFFFFu, gi, o);
                     }
-                    al = warp_sum(al); be = warp_sum(be); gr = warp_sum(gr); gi = warp_sum(gi);
-                    const R g = sqrt(gr * gr + gi * gi);
-                    if (g > tol * sqrt(al * be) && g > (R)0 && fmin(al, be) > floor2) {
+                    const R g2 = gr * gr + gi * gi;
+                    if (act && g2 > tol * tol * (al * be) && g2 > (R)0 && fmin(al, be) > floor2) {
                         rotated = 1;
-                        const R zeta = (be - al) / (2 * g);
-                        const R t = (zeta >= 0 ? (R)1 : (R)-1) / (fabs(zeta) + sqrt((R)1 + zeta * zeta));
-                        const R c = (R)1 / sqrt((R)1 + t * t), s = c * t;
-                        const R er = gr / g, ei = gi / g;
-                        for (int i = lane; i < rows; i += 32) {
+                        const R rg = rs_sqrt(g2);                    // 1 / |gamma|
+                        const R zeta = (be - al) * (R)0.5 * rg;
+                        const R t = fdiv(zeta >= 0 ? (R)1 : (R)-1, fabs(zeta) + sqrt((R)1 + zeta * zeta));
+                        const R c = rs_sqrt((R)1 + t * t), sn = c * t;
+                        const R er = gr * rg, ei = gi * rg;
+                        for (int i = gl; i < rows; i += g) {
                             const V x = a[i], y = b[i];
                             const R emx = er * y.x + ei * y.y, emy = er * y.y - ei * y.x;  // e^{-i phi} y
                             const R epx = er * x.x - ei * x.y, epy = er * x.y + ei * x.x;  // e^{+i phi} x
-                            a[i] = cmk<V>(c * x.x - s * emx, c * x.y - s * emy);
-                            b[i] = cmk<V>(s * epx + c * y.x, s * epy + c * y.y);
+                            a[i] = cmk<V>(c * x.x - sn * emx, c * x.y - sn * emy);
+                            b[i] = cmk<V>(sn * epx + c * y.x, sn * epy + c * y.y);
                         }
                     }
                 }
-                __syncthreads();
+                bsync<NT>();
             }
-            if (!__syncthreads_or(rotated)) return true;
+            ++sweeps;
+            if (!bsync_or<NT>(rotated)) return true;
         }
         return false;
     }
 
+    __device__ void release_big(bool locked) {
+        if (!locked) return;
+        bsync<NT>();
+        if (tid_ == 0) {
+            __threadfence_block();
+            atomicExch(S.big_lock, 0);
+        }
+    }
+
     // ---- two-site update on (q, q+1) -----------------------------------------------------------
+    // Shared-memory work area W, per update:  X (Jacobi matrix, ld x cols) | T (theta' copy, m x n;
+    // A and B are staged here first and read by the contraction, theta' is copied in afterwards)
+    // | sig2 | perm.  When that does not fit, X (if needed) and T go to the slot's global scratch
+    // and A, B are read from the site tensors.
     __device__ void update(int q, const V* g, bool right) {
+        bsync<NT>();  // pending gates written by thread 0, dims of the previous update
         const int cl = S.dims[q], cm = S.dims[q + 1], cr = S.dims[q + 2];
         const int m = 2 * cl, n = 2 * cr;
         const int rows = right ? m : n, cols = right ? n : m;
         const int ld = rows + 1;
-        V* X = ((uint64_t)ld * cols <= P.x_smem) ? S.X : xg;
+        const uint64_t ab = (uint64_t)m * cm + (uint64_t)cm * n;
+        const uint64_t treg = max((uint64_t)m * n, ab);
+        const uint64_t sgw = ((uint64_t)cols * (sizeof(R) + sizeof(int)) + sizeof(V) - 1) / sizeof(V);
+        const uint64_t need = (uint64_t)ld * cols + treg + sgw;
+        bool fast = need <= P.x_smem;
+        V* W = S.X;
+        bool locked = false;
+        if (!fast && NT == 32 && need <= P.x_big) {
+            // warp mode: borrow the CTA's large work area (bounded wait; the global path otherwise)
+            int got = 0;
+            if (tid_ == 0) {
+                for (int it = 0; it < (1 << 22); ++it) {
+                    if (atomicCAS(S.big_lock, 0, 1) == 0) { got = 1; break; }
+                    __nanosleep(256);
+                }
+                __threadfence_block();
+            }
+            got = __shfl_sync(0xFFFFFFFFu, got, 0);
+            if (got) { W = S.big; fast = true; locked = true; }
+        }
+        V* X = fast ? W : ((uint64_t)ld * cols <= P.x_smem ? S.X : xg);
+        V* T = fast ? W + (size_t)ld * cols : tcopy;
+        R* sig2 = fast ? reinterpret_cast<R*>(T + treg) : gsig2;
+        int* perm = reinterpret_cast<int*>(sig2 + cols);
         const V* A = site(q);
         const V* B = site(q + 1);
-        // theta'[(l,s),(t,r)] = sum_{s',t'} g[(s,t),(s',t')] sum_k A[l,s',k] B[k,t',r]
+        // fused gate: gate[(a,b),(s',t')] = sum_{s,t} g[(a,b),(s,t)] U_q[s,s'] U_{q+1}[t,t']
+        if (tid_ < 16) {
+            const int abi = tid_ >> 2, sp = (tid_ >> 1) & 1, tp = tid_ & 1;
+            const V* uq = S.pend + q * 4;
+            const V* ur = S.pend + (q + 1) * 4;
+            V acc = cmk<V>(0, 0);
+#pragma unroll
+            for (int st = 0; st < 4; ++st) {
+                const V w = cmul(uq[(st >> 1) * 2 + sp], ur[(st & 1) * 2 + tp]);
+                acc = cfma(g[abi * 4 + st], w, acc);
+            }
+            S.gate[tid_] = acc;
+        }
+        if (fast) {
+            V* As = T;
+            V* Bs = T + (size_t)m * cm;
+            for (int e = tid_; e < m * cm; e += NT) As[e] = A[e];
+            for (int e = tid_; e < cm * n; e += NT) Bs[e] = B[e];
+            A = As;
+            B = Bs;
+        }
+        bsync<NT>();
+        if (tid_ == 0) { reset_pend(q); reset_pend(q + 1); }
+        const V* gt = S.gate;
+        // theta'[(l,s),(t,r)] = sum_{s',t'} gate[(s,t),(s',t')] sum_k A[l,s',k] B[k,t',r]
         double fro = 0;
-        for (int e = threadIdx.x; e < cl * cr; e += NT) {
+        for (int e = tid_; e < cl * cr; e += NT) {
             const int l = e / cr, r = e - l * cr;
             V th[4];
 #pragma unroll
@@ -252,66 +384,85 @@ struct Engine {
             for (int st = 0; st < 4; ++st) {
                 V v = cmk<V>(0, 0);
 #pragma unroll
-                for (int u = 0; u < 4; ++u) v = cfma(g[st * 4 + u], th[u], v);
+                for (int u = 0; u < 4; ++u) v = cfma(gt[st * 4 + u], th[u], v);
                 const int i = l * 2 + (st >> 1), j = (st & 1) * cr + r;
                 fro += (double)v.x * v.x + (double)v.y * v.y;
-                tcopy[(size_t)i * n + j] = v;
+                if (!fast) T[(size_t)i * n + j] = v;
                 if (right) X[(size_t)j * ld + i] = v;
                 else X[(size_t)i * ld + j] = cmk<V>(v.x, -v.y);
             }
         }
-        fro = block_sum<NT>(fro, S.red);
+        if (fast) {  // A and B are consumed: keep theta' in T for the projection after the split
+            bsync<NT>();
+            for (int e = tid_; e < m * n; e += NT) {
+                const int i = e / n, j = e - i * n;
+                const V v = right ? X[(size_t)j * ld + i] : X[(size_t)i * ld + j];
+                T[e] = right ? v : cmk<V>(v.x, -v.y);
+            }
+        }
+        fro = block_sum<NT>(fro, S.red, tid_);
         const R eps = sizeof(R) == 4 ? (R)FLT_EPSILON : (R)DBL_EPSILON;
         const R fl = (R)4 * eps * sqrt((R)rows);
         const R floor2 = fl * fl * (R)fro;
         if (!jacobi(X, rows, cols, ld, floor2)) {
             status = QC_ENOCONV;
+            release_big(locked);
             return;
         }
         // singular values: column norms, then descending order (ties: lower index first)
-        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-        for (int j = wid; j < cols; j += NT / 32) {
-            const V* col = X + (size_t)j * ld;
-            R s = 0;
-            for (int i = lane; i < rows; i += 32) s = fma(col[i].x, col[i].x, fma(col[i].y, col[i].y, s));
-            s = warp_sum(s);
-            if (lane == 0) S.sig2[j] = s;
+        {
+            const int lane = tid_ & 31, wid = tid_ >> 5;
+            constexpr int NW = NT / 32;
+            const int cpw = (cols + NW - 1) / NW;
+            int G = 1;
+            while (G < cpw && G < 32) G <<= 1;
+            const int g = 32 / G, grp = lane / g, gl = lane - grp * g;
+            for (int base = wid * G; base < cols; base += NW * G) {
+                const int j = base + grp;
+                R sq = 0;
+                if (j < cols) {
+                    const V* col = X + (size_t)j * ld;
+                    for (int i = gl; i < rows; i += g) sq = fma(col[i].x, col[i].x, fma(col[i].y, col[i].y, sq));
+                }
+                for (int o = g >> 1; o > 0; o >>= 1) sq += __shfl_xor_sync(0xFFFFFFFFu, sq, o);
+                if (j < cols && gl == 0) sig2[j] = sq;
+            }
         }
-        __syncthreads();
-        for (int j = threadIdx.x; j < cols; j += NT) {
-            const R sj = S.sig2[j];
+        bsync<NT>();
+        for (int j = tid_; j < cols; j += NT) {
+            const R sj = sig2[j];
             int rk = 0;
             for (int k = 0; k < cols; ++k) {
-                const R sk = S.sig2[k];
+                const R sk = sig2[k];
                 rk += (sk > sj) || (sk == sj && k < j);
             }
-            S.perm[rk] = j;
+            perm[rk] = j;
         }
-        __syncthreads();
+        bsync<NT>();
         // truncation rule, FP64: smallest r >= 1 with discarded tail <= cutoff * total, r <= chi_max
-        if (threadIdx.x == 0) {
+        if (tid_ == 0) {
             double tot = 0;
             int nz = 0;
             for (int k = 0; k < cols; ++k) {
-                tot += (double)S.sig2[k];
-                nz += S.sig2[k] > floor2;
+                tot += (double)sig2[k];
+                nz += sig2[k] > floor2;
             }
             const double thr = P.cutoff * tot;
             int r = cols;
             double tail = 0;
-            while (r > 1 && tail + (double)S.sig2[S.perm[r - 1]] <= thr) {
-                tail += (double)S.sig2[S.perm[r - 1]];
+            while (r > 1 && tail + (double)sig2[perm[r - 1]] <= thr) {
+                tail += (double)sig2[perm[r - 1]];
                 --r;
             }
             while (r > P.chi_max || (r > 1 && r > nz)) {
-                tail += (double)S.sig2[S.perm[r - 1]];
+                tail += (double)sig2[perm[r - 1]];
                 --r;
             }
             double kept = 0;
-            for (int k = 0; k < r; ++k) kept += (double)S.sig2[S.perm[k]];
+            for (int k = 0; k < r; ++k) kept += (double)sig2[perm[k]];
             int dg = 0;
             if (r < cols) {
-                const double sa = sqrt((double)S.sig2[S.perm[r - 1]]), sb = sqrt((double)S.sig2[S.perm[r]]);
+                const double sa = sqrt((double)sig2[perm[r - 1]]), sb = sqrt((double)sig2[perm[r]]);
                 dg = (sb > 0 && sa / sb - 1.0 < 1e-8);
             }
             S.red[40] = tot > 0 ? tail / tot : 0.0;
@@ -319,58 +470,60 @@ struct Engine {
             S.red[42] = (double)r;
             S.red[43] = (double)dg;
         }
-        __syncthreads();
+        bsync<NT>();
         const int r = (int)S.red[42];
         disc += S.red[40];
         degen += (int)S.red[43];
         const R scale = (R)S.red[41];
         if (r > P.cap[q + 1]) {
             status = QC_ECAPACITY;
+            release_big(locked);
             return;
         }
         // normalise the kept columns to unit length (the orthonormal factor)
-        for (int e = threadIdx.x; e < r * rows; e += NT) {
+        for (int e = tid_; e < r * rows; e += NT) {
             const int k = e / rows, i = e - k * rows;
-            const int j = S.perm[k];
-            const R sg = S.sig2[j];
+            const int j = perm[k];
+            const R sg = sig2[j];
             const R inv = sg > (R)0 ? (R)1 / sqrt(sg) : (R)0;
             V* col = X + (size_t)j * ld;
             col[i] = cmk<V>(col[i].x * inv, col[i].y * inv);
         }
-        __syncthreads();
+        bsync<NT>();
         V* As = site(q);
         V* Bs = site(q + 1);
         if (right) {
             // A[q] = U (cl, 2, r);  A[q+1] = scale * U^H theta' (r, 2, cr)
-            for (int e = threadIdx.x; e < m * r; e += NT) {
+            for (int e = tid_; e < m * r; e += NT) {
                 const int i = e / r, k = e - i * r;
-                As[e] = X[(size_t)S.perm[k] * ld + i];
+                As[e] = X[(size_t)perm[k] * ld + i];
             }
-            for (int e = threadIdx.x; e < r * n; e += NT) {
+            for (int e = tid_; e < r * n; e += NT) {
                 const int k = e / n, j = e - k * n;
-                const V* u = X + (size_t)S.perm[k] * ld;
+                const V* u = X + (size_t)perm[k] * ld;
                 V acc = cmk<V>(0, 0);
-                for (int i = 0; i < m; ++i) acc = cfmac(u[i], tcopy[(size_t)i * n + j], acc);
+                for (int i = 0; i < m; ++i) acc = cfmac(u[i], T[(size_t)i * n + j], acc);
                 Bs[e] = cmk<V>(acc.x * scale, acc.y * scale);
             }
         } else {
             // A[q+1] = U'^H (r, 2, cr);  A[q] = scale * theta' U' (cl, 2, r)
-            for (int e = threadIdx.x; e < r * n; e += NT) {
+            for (int e = tid_; e < r * n; e += NT) {
                 const int k = e / n, j = e - k * n;
-                const V u = X[(size_t)S.perm[k] * ld + j];
+                const V u = X[(size_t)perm[k] * ld + j];
                 Bs[e] = cmk<V>(u.x, -u.y);
             }
-            for (int e = threadIdx.x; e < m * r; e += NT) {
+            for (int e = tid_; e < m * r; e += NT) {
                 const int i = e / r, k = e - i * r;
-                const V* u = X + (size_t)S.perm[k] * ld;
+                const V* u = X + (size_t)perm[k] * ld;
                 V acc = cmk<V>(0, 0);
-                for (int j = 0; j < n; ++j) acc = cfma(tcopy[(size_t)i * n + j], u[j], acc);
+                for (int j = 0; j < n; ++j) acc = cfma(T[(size_t)i * n + j], u[j], acc);
                 As[e] = cmk<V>(acc.x * scale, acc.y * scale);
             }
         }
-        __syncthreads();
-        if (threadIdx.x == 0) S.dims[q + 1] = r;
-        __syncthreads();
+        bsync<NT>();
+        release_big(locked);
+        if (tid_ == 0) S.dims[q + 1] = r;
+        bsync<NT>();
         chi_peak = max(chi_peak, r);
         ++nupd;
         {
@@ -383,17 +536,26 @@ struct Engine {
     // ---- readout on site q (the orthogonality centre) ------------------------------------------
     // returns the outcome, or -1 when the shot ends (rejected / error)
     __device__ int readout(int q, uint32_t rid, bool is_meas, uint64_t shot, int64_t src) {
+        bsync<NT>();  // pending gates written by thread 0
         const int cl = S.dims[q], cr = S.dims[q + 1];
         V* a = site(q);
+        const V* u = S.pend + q * 4;
+        const V g00 = u[0], g01 = u[1], g10 = u[2], g11 = u[3];
         double p0 = 0, p1 = 0;
-        for (int e = threadIdx.x; e < cl * cr; e += NT) {
+        for (int e = tid_; e < cl * cr; e += NT) {
             const int l = e / cr, r = e - l * cr;
-            const V x = a[(l * 2) * cr + r], y = a[(l * 2 + 1) * cr + r];
+            V* px = a + (l * 2) * cr + r;
+            V* py = px + cr;
+            const V x0 = *px, y0 = *py;
+            const V x = cfma(g00, x0, cmul(g01, y0)), y = cfma(g10, x0, cmul(g11, y0));
+            *px = x;
+            *py = y;
             p0 += (double)x.x * x.x + (double)x.y * x.y;
             p1 += (double)y.x * y.x + (double)y.y * y.y;
         }
-        p0 = block_sum<NT>(p0, S.red);
-        p1 = block_sum<NT>(p1, S.red);
+        p0 = block_sum<NT>(p0, S.red, tid_);
+        p1 = block_sum<NT>(p1, S.red, tid_);
+        if (tid_ == 0) reset_pend(q);
         const double tot = p0 + p1;
         const double pr1 = tot > 0 ? p1 / tot : 0.0;
         int outcome;
@@ -401,7 +563,7 @@ struct Engine {
             if (is_meas) {
                 const double lim = P.precision == QC_C128 ? 1e-10 : 1e-5;
                 if (pr1 > lim) {
-                    if (threadIdx.x == 0) atomicCAS(P.ref_status, 0, (int)(src + 1));
+                    if (tid_ == 0) atomicCAS(P.ref_status, 0, (int)(src + 1));
                 }
                 outcome = 0;
             } else {
@@ -424,7 +586,7 @@ struct Engine {
         }
         const R sc = (R)(1.0 / sqrt(po));
         const bool flip = (!is_meas) && outcome == 1;  // reset to |0>: project on 1 then X
-        for (int e = threadIdx.x; e < cl * cr; e += NT) {
+        for (int e = tid_; e < cl * cr; e += NT) {
             const int l = e / cr, r = e - l * cr;
             V* x0 = a + (l * 2) * cr + r;
             V* x1 = x0 + cr;
@@ -434,7 +596,7 @@ struct Engine {
             else if (flip) { *x0 = kv; *x1 = cmk<V>(0, 0); }
             else { *x0 = cmk<V>(0, 0); *x1 = kv; }
         }
-        __syncthreads();
+        bsync<NT>();
         return outcome;
     }
 
@@ -445,8 +607,8 @@ struct Engine {
         const uint64_t need = (uint64_t)cap2 * cap2 * 3;
         V* E = (need <= P.x_smem) ? S.X : xg;
         V* T1 = E + (size_t)cap2 * cap2;
-        if (threadIdx.x == 0) E[0] = cmk<V>(1, 0);
-        __syncthreads();
+        if (tid_ == 0) E[0] = cmk<V>(1, 0);
+        bsync<NT>();
         const V* refsite = P.ref;
         for (int q = 0; q < P.nq; ++q) {
             const int ca = P.ref_dims[q], ca2 = P.ref_dims[q + 1];
@@ -454,15 +616,15 @@ struct Engine {
             const V* Aq = site(q);
             const V* Rq = refsite + P.off[q];
             // T1[a][s][b'] = sum_b E[a][b] A[b][s][b']
-            for (int e = threadIdx.x; e < ca * 2 * cb2; e += NT) {
+            for (int e = tid_; e < ca * 2 * cb2; e += NT) {
                 const int a_ = e / (2 * cb2), rest = e - a_ * 2 * cb2;
                 V acc = cmk<V>(0, 0);
                 for (int b = 0; b < cb; ++b) acc = cfma(E[(size_t)a_ * cb + b], Aq[(size_t)b * 2 * cb2 + rest], acc);
                 T1[e] = acc;
             }
-            __syncthreads();
+            bsync<NT>();
             // E'[a'][b'] = sum_{a,s} conj(R[a][s][a']) T1[a][s][b']
-            for (int e = threadIdx.x; e < ca2 * cb2; e += NT) {
+            for (int e = tid_; e < ca2 * cb2; e += NT) {
                 const int ap = e / cb2, bp = e - ap * cb2;
                 V acc = cmk<V>(0, 0);
                 for (int a_ = 0; a_ < ca; ++a_)
@@ -470,10 +632,10 @@ struct Engine {
                         acc = cfmac(Rq[((size_t)a_ * 2 + s) * ca2 + ap], T1[((size_t)a_ * 2 + s) * cb2 + bp], acc);
                 E[e] = acc;
             }
-            __syncthreads();
+            bsync<NT>();
         }
         const V ov = E[0];
-        __syncthreads();
+        bsync<NT>();
         return make_double2((double)ov.x, (double)ov.y);
     }
 
@@ -482,20 +644,20 @@ struct Engine {
         const int cl = dims[q], cr = dims[q + 1];
         const V* a = base + P.off[q];
         double s = 0;
-        for (int e = threadIdx.x; e < cl * 2 * cr; e += NT) s += (double)a[e].x * a[e].x + (double)a[e].y * a[e].y;
-        return block_sum<NT>(s, S.red);
+        for (int e = tid_; e < cl * 2 * cr; e += NT) s += (double)a[e].x * a[e].x + (double)a[e].y * a[e].y;
+        return block_sum<NT>(s, S.red, tid_);
     }
 
     // ---- faults of one shot into S.fch / S.fcode (sorted by channel); returns the count ------
     __device__ int faults(uint64_t shot) {
-        __shared__ int nf;
-        if (threadIdx.x == 0) nf = 0;
-        __syncthreads();
+        int& nf = *S.nf;
+        if (tid_ == 0) nf = 0;
+        bsync<NT>();
         if (P.reference) return 0;
         if (P.weight < 0) {
             const uint32_t w = (uint32_t)(shot >> 6), lane = (uint32_t)(shot & 63);
             const uint32_t ng = (P.nchan + 3) / 4;
-            for (uint32_t g = threadIdx.x; g < ng; g += NT) {
+            for (uint32_t g = tid_; g < ng; g += NT) {
                 const U4 u = philox(g, w, 0, TAG_WORD, P.k0, P.k1);
 #pragma unroll
                 for (uint32_t j = 0; j < 4; ++j) {
@@ -511,8 +673,8 @@ struct Engine {
                     }
                 }
             }
-            __syncthreads();
-            if (threadIdx.x == 0) {  // insertion sort by channel
+            bsync<NT>();
+            if (tid_ == 0) {  // insertion sort by channel
                 const int cnt = min(nf, MAXF);
                 for (int i = 1; i < cnt; ++i) {
                     const uint32_t c = S.fch[i];
@@ -523,7 +685,7 @@ struct Engine {
                     S.fcode[k] = d;
                 }
             }
-        } else if (threadIdx.x == 0) {
+        } else if (tid_ == 0) {
             uint32_t draw = 0;
             const uint32_t M = P.nchan, W = (uint32_t)P.weight;
             int cnt = 0;
@@ -542,44 +704,50 @@ struct Engine {
             for (int k = 0; k < min(cnt, MAXF); ++k) S.fcode[k] = (uint8_t)exact_code(P.chan_kind[S.fch[k]], S.fch[k], shot, P.k0, P.k1);
             nf = cnt;
         }
-        __syncthreads();
+        bsync<NT>();
         const int out = nf;
-        __syncthreads();
+        bsync<NT>();
         return out;
     }
 
     __device__ void run(uint64_t task) {
         const uint64_t shot = P.reference ? 0 : P.shots[task];
-        status = 0; disc = 0; degen = 0; chi_peak = 1; nupd = 0; abort_op = -1; flops = 0;
-        for (int q = threadIdx.x; q <= P.nq; q += NT) S.dims[q] = 1;
-        for (int q = threadIdx.x; q < P.nq; q += NT) {
+        status = 0; disc = 0; degen = 0; chi_peak = 1; nupd = 0; abort_op = -1; flops = 0; sweeps = 0;
+        for (int q = tid_; q <= P.nq; q += NT) S.dims[q] = 1;
+        for (int q = tid_; q < P.nq; q += NT) {
             V* a = site(q);
             a[0] = cmk<V>(1, 0);
             a[1] = cmk<V>(0, 0);
+            reset_pend(q);
         }
-        __syncthreads();
+        bsync<NT>();
         const int nf = faults(shot);
         if (nf > MAXF) status = QC_ECAPACITY;
-        int fptr = 0;
         for (uint32_t base = 0; base < P.nops && status == 0; base += OPCH) {
             const uint32_t cnt = min((uint32_t)OPCH, P.nops - base);
-            for (uint32_t i = threadIdx.x; i < cnt; i += NT) S.ops[i] = P.prog[base + i];
-            __syncthreads();
+            for (uint32_t i = tid_; i < cnt; i += NT) S.ops[i] = P.prog[base + i];
+            bsync<NT>();
             for (uint32_t i = 0; i < cnt && status == 0; ++i) {
                 const MpsOp op = S.ops[i];
                 switch (op.kind) {
                     case M_G1: {
                         const V* g = P.g1 + op.a * 4;
-                        apply1(op.q, g[0], g[1], g[2], g[3]);
+                        defer1(op.q, g[0], g[1], g[2], g[3]);
                         break;
                     }
                     case M_CH1:
                     case M_CH2: {
-                        if (fptr < nf && S.fch[fptr] == op.a) {
-                            const uint32_t code = S.fcode[fptr];
-                            ++fptr;
-                            if (op.kind == M_CH1) apply_pauli(op.q, code);
-                            else { apply_pauli(op.q, code >> 2); apply_pauli(op.b, code & 3); }
+                        // the schedule may visit channels out of text order: binary search the
+                        // shot's faults (sorted by channel)
+                        int lo = 0, hi = nf;
+                        while (lo < hi) {
+                            const int mid = (lo + hi) >> 1;
+                            if (S.fch[mid] < op.a) lo = mid + 1; else hi = mid;
+                        }
+                        if (lo < nf && S.fch[lo] == op.a) {
+                            const uint32_t code = S.fcode[lo];
+                            if (op.kind == M_CH1) defer_pauli(op.q, code);
+                            else { defer_pauli(op.q, code >> 2); defer_pauli(op.b, code & 3); }
                         }
                         break;
                     }
@@ -594,9 +762,18 @@ struct Engine {
                     default: break;
                 }
             }
-            __syncthreads();
+            bsync<NT>();
         }
-        // finish
+        // finish: apply the gates still pending, then compare with the reference
+        if (status == 0)
+            for (int q = 0; q < P.nq; ++q) {
+                bsync<NT>();
+                const V* u = S.pend + q * 4;
+                const bool ident = u[0].x == (R)1 && u[0].y == (R)0 && u[1].x == (R)0 && u[1].y == (R)0 &&
+                                   u[2].x == (R)0 && u[2].y == (R)0 && u[3].x == (R)1 && u[3].y == (R)0;
+                if (!ident) flush_site(q);
+            }
+        bsync<NT>();
         double fid = -1.0;
         int lerr = 0;
         if (status == 0 && !P.reference) {
@@ -608,10 +785,11 @@ struct Engine {
             if (!(tau > 0)) tau = P.precision == QC_C128 ? 1e-8 : fmax(1e-3, 10.0 * (P.ref_disc + disc));
             lerr = (1.0 - fid) > tau;
         }
-        if (threadIdx.x == 0) {
+        if (tid_ == 0) {
             if (P.reference) {
                 for (int q = 0; q <= P.nq; ++q) P.ref_dims_out[q] = S.dims[q];
                 *P.ref_disc_out = disc;
+                *P.ref_chi_out = chi_peak;
                 if (status != 0) atomicCAS(P.ref_status, 0, -1000 + status);
             } else {
                 const int wb = min(nf, P.wmax);
@@ -633,47 +811,77 @@ struct Engine {
                     res.degenerate_cuts = degen;
                     res.n_updates = nupd;
                     res.alg_flops = flops;
+                    res.sweeps = sweeps;
                     P.per_shot[task] = res;
                 }
             }
         }
-        __syncthreads();
+        bsync<NT>();
     }
 };
 
 template <typename R, int NT>
-__global__ void __launch_bounds__(NT, 1) engine_kernel(const EngineParams<R> P) {
+__host__ __device__ size_t engine_smem(const EngineParams<R>& P);
+
+// Shared-memory layout of one engine's region (X, program chunk, reductions, bonds, pending gates,
+// fused gate, faults).
+template <typename R>
+__device__ unsigned char* carve(Shared<R>& S, unsigned char* p, const EngineParams<R>& P) {
     using V = typename VecOf<R>::T;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    Shared<R> S;
-    unsigned char* p = smem_raw;
     S.X = reinterpret_cast<V*>(p); p += (size_t)P.x_smem * sizeof(V);
     S.ops = reinterpret_cast<MpsOp*>(p); p += OPCH * sizeof(MpsOp);
     S.red = reinterpret_cast<double*>(p); p += 64 * sizeof(double);
-    S.sig2 = reinterpret_cast<R*>(p); p += (size_t)2 * P.chi_max * sizeof(R) + 16;
-    S.perm = reinterpret_cast<int*>(p); p += (size_t)2 * P.chi_max * sizeof(int);
     S.dims = reinterpret_cast<int*>(p); p += (size_t)(P.nq + 1) * sizeof(int);
+    p = reinterpret_cast<unsigned char*>(((uintptr_t)p + 15) & ~(uintptr_t)15);
+    S.pend = reinterpret_cast<V*>(p); p += (size_t)P.nq * 4 * sizeof(V);
+    S.gate = reinterpret_cast<V*>(p); p += 16 * sizeof(V);
     S.fch = reinterpret_cast<uint32_t*>(p); p += MAXF * sizeof(uint32_t);
-    S.fcode = reinterpret_cast<uint8_t*>(p);
+    S.nf = reinterpret_cast<int*>(p); p += 16;
+    S.fcode = reinterpret_cast<uint8_t*>(p); p += MAXF;
+    return reinterpret_cast<unsigned char*>(((uintptr_t)p + 15) & ~(uintptr_t)15);
+}
 
-    Engine<R, NT> eng(P, S, blockIdx.x);
-    __shared__ unsigned long long task_s;
+// Persistent engine.  CTA mode (NT > 32): the CTA is one engine.  Warp mode (NT = 32): every warp
+// of the CTA is an engine with its own shot slot, and the warps share one large work area.
+template <typename R, int NT>
+__global__ void __launch_bounds__(NT == 32 ? 256 : NT, NT == 32 ? 1 : (NT == 128 ? 4 : (NT == 256 ? 2 : 1)))
+engine_kernel(const EngineParams<R> P) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int engines = (NT == 32) ? (int)(blockDim.x >> 5) : 1;
+    const int e = (NT == 32) ? (int)(threadIdx.x >> 5) : 0;
+    const int tid = (NT == 32) ? (int)(threadIdx.x & 31) : (int)threadIdx.x;
+    const size_t region = (engine_smem<R, NT>(P) + 15) & ~(size_t)15;
+    Shared<R> S;
+    carve<R>(S, smem_raw + region * e, P);
+    S.big = reinterpret_cast<typename VecOf<R>::T*>(smem_raw + region * engines);
+    S.big_lock = reinterpret_cast<int*>(smem_raw + region * engines + (size_t)P.x_big * sizeof(typename VecOf<R>::T));
+    if (NT == 32 && threadIdx.x == 0) *S.big_lock = 0;
+    __syncthreads();
+    Engine<R, NT> eng(P, S, blockIdx.x * engines + e, tid);
     for (;;) {
-        if (threadIdx.x == 0) task_s = atomicAdd(P.next_task, 1ull);
-        __syncthreads();
-        const unsigned long long task = task_s;
-        __syncthreads();
+        unsigned long long task = 0;
+        if (NT == 32) {
+            if (tid == 0) task = atomicAdd(P.next_task, 1ull);
+            task = __shfl_sync(0xFFFFFFFFu, task, 0);
+        } else {
+            __shared__ unsigned long long task_s;
+            if (tid == 0) task_s = atomicAdd(P.next_task, 1ull);
+            __syncthreads();
+            task = task_s;
+            __syncthreads();
+        }
         if (task >= P.ntasks) break;
         eng.run(task);
     }
 }
 
+// Bytes of one engine's region.
 template <typename R, int NT>
-size_t engine_smem(const EngineParams<R>& P) {
+__host__ __device__ size_t engine_smem(const EngineParams<R>& P) {
     using V = typename VecOf<R>::T;
     return (size_t)P.x_smem * sizeof(V) + OPCH * sizeof(MpsOp) + 64 * sizeof(double) +
-           (size_t)2 * P.chi_max * sizeof(R) + 16 + (size_t)2 * P.chi_max * sizeof(int) +
-           (size_t)(P.nq + 1) * sizeof(int) + MAXF * sizeof(uint32_t) + MAXF + 16;
+           (size_t)(P.nq + 1) * sizeof(int) + 16 + (size_t)P.nq * 4 * sizeof(V) + 16 * sizeof(V) +
+           MAXF * sizeof(uint32_t) + 16 + MAXF + 16;
 }
 
 // ---- gate tables ------------------------------------------------------------------------------
@@ -745,7 +953,6 @@ qc_status device_tables(DeviceTables** out) {
 
 constexpr int NT_F = 512;
 constexpr int NT_D = 256;
-constexpr size_t SMEM_BUDGET = 200 * 1024;
 
 }  // namespace
 
@@ -773,8 +980,25 @@ static SlotLayout slot_layout(int n, int chi_max) {
     return L;
 }
 
-// Host driver shared by mps_sample_batch and the serving loop.
+// Shared-memory configuration of one engine variant: how much of theta's Jacobi matrix X fits in
+// shared memory next to the fixed per-CTA arrays, within the variant's budget.
 template <typename R, int NT>
+static size_t configure_smem(EngineParams<R>& P, size_t budget, uint64_t x_full) {
+    using V = typename VecOf<R>::T;
+    P.x_smem = 0;
+    const uint64_t fixed = engine_smem<R, NT>(P);
+    uint64_t x_cap = (budget - std::min<uint64_t>(budget, fixed)) / sizeof(V);
+    P.x_smem = (uint32_t)(std::min<uint64_t>(x_cap, x_full) & ~1ull);  // keeps the next region 16-byte aligned
+    return engine_smem<R, NT>(P);
+}
+
+// Host driver shared by mps_sample_batch and the serving loop.
+//
+// chi-bucketed variants: the reference run tells the bond dimensions the circuit reaches.  When
+// they stay small (chi_peak <= 64, theta at most 128 x 128) every shot gets one warp of its own
+// (NT = 32, many shot slots per SM, the common small updates latency-bound per warp); otherwise
+// one CTA of NT_BIG threads works on each shot.
+template <typename R, int NT_BIG>
 static qc_status run_engine(CircuitImpl& c, qc_noise noise, const uint64_t* shots_dev, uint64_t nshots,
                             qc_mps_params prm, unsigned long long* counts_dev, int wmax,
                             qc_shot_result* per_shot, cudaStream_t s, int max_slots) {
@@ -787,21 +1011,18 @@ static qc_status run_engine(CircuitImpl& c, qc_noise noise, const uint64_t* shot
     if (st != QC_OK) return st;
     const SlotLayout L = slot_layout(c.n, prm.chi_max);
     const int chi = L.chi_cap;
-    // X in shared memory up to the budget
     const uint64_t x_full = (uint64_t)(2 * chi + 1) * (2 * chi);
     const uint64_t over_full = (uint64_t)chi * chi * 3;
-    EngineParams<R> P{};
-    P.chi_max = chi;
-    uint64_t fixed = engine_smem<R, NT>(P) + (uint64_t)(c.n + 1) * sizeof(int);
-    uint64_t x_cap = (SMEM_BUDGET - std::min<uint64_t>(SMEM_BUDGET, fixed)) / sizeof(V);
-    x_cap = std::min<uint64_t>(x_cap, std::max(x_full, over_full));
     const uint64_t xg_elems = std::max(x_full, over_full);
-    const uint64_t scratch_stride = xg_elems + (uint64_t)(2 * chi) * (2 * chi);
+    const uint64_t sg_elems = ((uint64_t)(2 * chi) * (sizeof(R) + sizeof(int)) + sizeof(V) - 1) / sizeof(V) + 2;
+    const uint64_t scratch_stride = xg_elems + (uint64_t)(2 * chi) * (2 * chi) + sg_elems;
 
     int dev = 0, nsm = 0;
     QC_CUDA(cudaGetDevice(&dev));
     QC_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
 
+    EngineParams<R> P{};
+    P.chi_max = chi;
     P.prog = dc->mps;
     P.nops = (uint32_t)c.mps.size();
     P.nq = c.n;
@@ -812,7 +1033,6 @@ static qc_status run_engine(CircuitImpl& c, qc_noise noise, const uint64_t* shot
     P.slot_stride = L.stride;
     P.scratch_stride = scratch_stride;
     P.xg_elems = xg_elems;
-    P.x_smem = (uint32_t)x_cap;
     P.cutoff = prm.cutoff;
     P.k0 = (uint32_t)noise.seed;
     P.k1 = (uint32_t)(noise.seed >> 32);
@@ -823,7 +1043,6 @@ static qc_status run_engine(CircuitImpl& c, qc_noise noise, const uint64_t* shot
     P.precision = prm.precision;
     P.wmax = wmax;
     P.sweep_cap = sizeof(R) == 4 ? 40 : 60;
-    // final orthogonality centre of the program
     {
         int center = 0;
         for (const MpsOp& o : c.mps) {
@@ -832,14 +1051,6 @@ static qc_status run_engine(CircuitImpl& c, qc_noise noise, const uint64_t* shot
         }
         P.final_center = center;
     }
-    const size_t smem = engine_smem<R, NT>(P);
-    QC_CUDA(cudaFuncSetAttribute(engine_kernel<R, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int per_sm = 0;
-    QC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, engine_kernel<R, NT>, NT, smem));
-    if (per_sm < 1) return fail(QC_ENOMEM, "engine does not fit on an SM (smem %zu)", smem);
-    uint64_t slots = std::min<uint64_t>(nshots ? nshots : 1, (uint64_t)per_sm * nsm);
-    if (max_slots > 0) slots = std::min<uint64_t>(slots, (uint64_t)max_slots);
-    if (slots < 1) slots = 1;
 
     // 1. the noiseless reference state, computed once per (device, chi_max, cutoff, precision)
     RefState* ref = nullptr;
@@ -863,6 +1074,9 @@ static qc_status run_engine(CircuitImpl& c, qc_noise noise, const uint64_t* shot
             if (e != cudaSuccess) out = cuda_fail(e, "reference workspace");
             if (out == QC_OK) {
                 EngineParams<R> Pr = P;
+                Pr.x_big = 0;
+                const size_t smem = configure_smem<R, NT_BIG>(Pr, 200 * 1024, std::max(x_full, over_full));
+                e = cudaFuncSetAttribute(engine_kernel<R, NT_BIG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
                 Pr.reference = 1;
                 Pr.mps = reinterpret_cast<V*>(rs.state);
                 Pr.off = rs.off;
@@ -871,18 +1085,22 @@ static qc_status run_engine(CircuitImpl& c, qc_noise noise, const uint64_t* shot
                 Pr.ntasks = 1;
                 Pr.next_task = reinterpret_cast<unsigned long long*>(tmp);
                 Pr.ref_status = reinterpret_cast<int*>(tmp + 8);
+                Pr.ref_chi_out = reinterpret_cast<int*>(tmp + 12);
                 Pr.ref_disc_out = reinterpret_cast<double*>(tmp + 16);
                 Pr.ref_dims_out = rs.dims;
                 Pr.counts = nullptr;
-                engine_kernel<R, NT><<<1, NT, smem, s>>>(Pr);
-                e = cudaGetLastError();
-                int st_h = 0;
-                if (e == cudaSuccess) e = cudaMemcpyAsync(&st_h, Pr.ref_status, sizeof(int), cudaMemcpyDeviceToHost, s);
+                if (e == cudaSuccess) {
+                    engine_kernel<R, NT_BIG><<<1, NT_BIG, smem, s>>>(Pr);
+                    e = cudaGetLastError();
+                }
+                int st_h[2] = {0, 0};
+                if (e == cudaSuccess) e = cudaMemcpyAsync(st_h, Pr.ref_status, 2 * sizeof(int), cudaMemcpyDeviceToHost, s);
                 if (e == cudaSuccess) e = cudaMemcpyAsync(&rs.disc, Pr.ref_disc_out, sizeof(double), cudaMemcpyDeviceToHost, s);
                 if (e == cudaSuccess) e = cudaStreamSynchronize(s);
                 if (e != cudaSuccess) out = cuda_fail(e, "reference run");
-                else if (st_h > 0) out = fail(QC_EINVAL, "measurement at instruction %d is not deterministically 0 in the noiseless circuit", st_h - 1);
-                else if (st_h < 0) out = fail((qc_status)(st_h + 1000), "reference run failed (status %d)", st_h + 1000);
+                else if (st_h[0] > 0) out = fail(QC_EINVAL, "measurement at instruction %d is not deterministically 0 in the noiseless circuit", st_h[0] - 1);
+                else if (st_h[0] < 0) out = fail((qc_status)(st_h[0] + 1000), "reference run failed (status %d)", st_h[0] + 1000);
+                rs.chi_peak = st_h[1];
                 if (out == QC_OK) {
                     const int q = P.final_center;
                     std::vector<int> rd(c.n + 1);
@@ -910,7 +1128,60 @@ static qc_status run_engine(CircuitImpl& c, qc_noise noise, const uint64_t* shot
     }
     if (nshots == 0) return QC_OK;
 
-    // 2. the shots: slots' site tensors and split scratch
+    // 2. the shots: the variant (threads per shot, shared-memory budget per shot) follows the
+    //    reference run's chi_peak; QCMPS_ENGINE = warp | cta128 | cta256 | cta and QCMPS_SMEM_KB
+    //    override the choice for tuning.
+    const char* force = getenv("QCMPS_ENGINE");
+    int variant = ref->chi_peak <= 64 ? 32 : NT_BIG;
+    if (force && !strcmp(force, "warp")) variant = 32;
+    if (force && !strcmp(force, "cta128")) variant = 128;
+    if (force && !strcmp(force, "cta256")) variant = 256;
+    if (force && !strcmp(force, "cta")) variant = NT_BIG;
+    const char* kb = getenv("QCMPS_SMEM_KB");
+    const int kbv = kb ? atoi(kb) : 0;
+    const char* wv = getenv("QCMPS_WARPS");
+    const char* bv = getenv("QCMPS_BIG_KB");
+    size_t smem;
+    int nt = variant;
+    int engines = 1;  // engines (shot slots) per CTA
+    const void* fn;
+    const uint64_t xf = std::max(x_full, over_full);
+    if (variant == 32) {
+        // warp mode: `engines` warps per CTA, each with its own work area, plus one shared large area
+        // measured on the 49-qubit workload: one warp per CTA with 24 KB (9 shot slots per SM)
+        // beats sharing a large area between warps (contention) and larger per-warp areas (fewer
+        // slots)
+        engines = (wv && atoi(wv) >= 1 && atoi(wv) <= 8) ? atoi(wv) : 1;
+        const size_t per = configure_smem<R, 32>(P, (kbv >= 8 && kbv <= 200 ? kbv : 24) * 1024, xf);
+        const size_t region = (per + 15) & ~(size_t)15;
+        const size_t big_budget = (bv && atoi(bv) >= 0) ? (size_t)atoi(bv) * 1024 : 0;
+        size_t room = 227 * 1024 > region * engines + 16 ? 227 * 1024 - region * engines - 16 : 0;
+        if (engines == 1) room = 0;  // nobody to share with
+        room = std::min(room, big_budget);
+        P.x_big = (uint32_t)std::min<uint64_t>((room / sizeof(V)) & ~1ull, 4 * xf);
+        smem = region * engines + (size_t)P.x_big * sizeof(V) + 16;
+        fn = (const void*)engine_kernel<R, 32>;
+        nt = 32 * engines;
+    } else if (variant == 128) {
+        smem = configure_smem<R, 128>(P, (kbv >= 8 && kbv <= 200 ? kbv : 72) * 1024, xf);
+        fn = (const void*)engine_kernel<R, 128>;
+    } else if (variant == 256) {
+        smem = configure_smem<R, 256>(P, (kbv >= 8 && kbv <= 200 ? kbv : 100) * 1024, xf);
+        fn = (const void*)engine_kernel<R, 256>;
+    } else {
+        smem = configure_smem<R, NT_BIG>(P, 200 * 1024, xf);
+        fn = (const void*)engine_kernel<R, NT_BIG>;
+        nt = NT_BIG;
+    }
+    QC_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    QC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, nt, smem));
+    if (per_sm < 1) return fail(QC_ENOMEM, "engine does not fit on an SM (smem %zu)", smem);
+    uint64_t ctas = std::min<uint64_t>((nshots + engines - 1) / engines, (uint64_t)per_sm * nsm);
+    if (max_slots > 0) ctas = std::min<uint64_t>(ctas, std::max<uint64_t>(1, (uint64_t)max_slots / engines));
+    if (ctas < 1) ctas = 1;
+    const uint64_t slots = ctas * engines;
+
     const uint64_t mps_elems = slots * L.stride;
     const uint64_t scr_elems = slots * scratch_stride;
     char* ws = nullptr;
@@ -937,7 +1208,10 @@ static qc_status run_engine(CircuitImpl& c, qc_noise noise, const uint64_t* shot
         P.next_task = reinterpret_cast<unsigned long long*>(ws);
         P.per_shot = per_shot;
         P.counts = counts_dev;
-        engine_kernel<R, NT><<<(unsigned)slots, NT, smem, s>>>(P);
+        if (variant == 32) engine_kernel<R, 32><<<(unsigned)ctas, 32 * engines, smem, s>>>(P);
+        else if (variant == 128) engine_kernel<R, 128><<<(unsigned)ctas, 128, smem, s>>>(P);
+        else if (variant == 256) engine_kernel<R, 256><<<(unsigned)ctas, 256, smem, s>>>(P);
+        else engine_kernel<R, NT_BIG><<<(unsigned)ctas, NT_BIG, smem, s>>>(P);
         e = cudaGetLastError();
         if (e != cudaSuccess) { out = cuda_fail(e, "engine"); break; }
     } while (0);
@@ -966,7 +1240,7 @@ qc_status shot_footprint(const CircuitImpl& c, qc_mps_params prm, uint64_t* byte
     const SlotLayout L = slot_layout(c.n, std::max(1, prm.chi_max));
     const int chi = L.chi_cap;
     const uint64_t x_full = std::max((uint64_t)(2 * chi + 1) * (2 * chi), (uint64_t)chi * chi * 3);
-    const uint64_t scratch = x_full + (uint64_t)(2 * chi) * (2 * chi);
+    const uint64_t scratch = x_full + (uint64_t)(2 * chi) * (2 * chi) + (uint64_t)(2 * chi) + 2;
     const uint64_t es = prm.precision == QC_C128 ? 16 : 8;
     *bytes = (L.stride + scratch) * es;
     return QC_OK;

@@ -76,6 +76,7 @@ struct RefState {
     int* cap = nullptr;        // [n+1] bond capacities, device
     uint64_t* off = nullptr;   // [n+1] site offsets, device
     double disc = 0, norm = 0;
+    int chi_peak = 0;
 };
 
 struct CircuitImpl {

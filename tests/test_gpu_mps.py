@@ -60,8 +60,11 @@ def _compare(res, ref, ftol, allow_flip=0):
     return flips
 
 
-def test_c128_d3_workload_matches_oracle():
-    """17-qubit d=3-shaped circuit, chi_max 32, cutoff 1e-12, complex128 (exact here)."""
+@pytest.mark.parametrize("variant", ["warp", "cta"])
+def test_c128_d3_workload_matches_oracle(variant, monkeypatch):
+    """17-qubit d=3-shaped circuit, chi_max 32, cutoff 1e-12, complex128 (exact here); both the
+    one-warp-per-shot and the one-CTA-per-shot engine variants."""
+    monkeypatch.setenv("QCMPS_ENGINE", variant)
     q = lib_ready()
     text = workload_circuit("d3_17q_12l")
     c = q.Circuit(text)
@@ -77,7 +80,9 @@ def test_c128_d3_workload_matches_oracle():
     assert res[res["status"] == 0]["chi_peak"].max() <= 32
 
 
-def test_c64_d3_workload_matches_oracle():
+@pytest.mark.parametrize("variant", ["warp", "cta"])
+def test_c64_d3_workload_matches_oracle(variant, monkeypatch):
+    monkeypatch.setenv("QCMPS_ENGINE", variant)
     q = lib_ready()
     text = workload_circuit("d3_17q_12l")
     c = q.Circuit(text)
@@ -141,8 +146,9 @@ def test_empty_batch_and_bad_params():
         q.mps_sample_batch(bad, dev_shots([0]), p=0.0, seed=0, chi_max=4, cutoff=0.0)
 
 
-def test_d5_workload_c64_sampled_shots():
-    """49-qubit, 60-layer workload, chi_max 64, c64, in the benchmark's launch: a few survivors
+@pytest.mark.parametrize("chi_max", [64, 256])
+def test_d5_workload_c64_sampled_shots(chi_max):
+    """49-qubit, 60-layer workload, c64, in the benchmark's launch (chi_max 256): a few survivors
     recomputed by the FP64 oracle MPS."""
     q = lib_ready()
     text = workload_circuit("d5_49q_60l")
@@ -150,9 +156,10 @@ def test_d5_workload_c64_sampled_shots():
     p, seed = 1e-3, 0
     shots = _survivors(q, c, p, seed, 64 * 4096)[:32]
     assert len(shots) >= 8
-    _, res = q.mps_sample_batch(c, dev_shots(shots), p=p, seed=seed, chi_max=64, cutoff=1e-10, precision=q.QC_C64)
+    _, res = q.mps_sample_batch(c, dev_shots(shots), p=p, seed=seed, chi_max=chi_max, cutoff=1e-10,
+                                precision=q.QC_C64)
     pick = [int(s) for s in shots[:4]]
-    ref = _oracle_results(text, pick, p=p, seed=seed, engine="mps", chi_max=64, cutoff=1e-10)
+    ref = _oracle_results(text, pick, p=p, seed=seed, engine="mps", chi_max=chi_max, cutoff=1e-10)
     sub = res[np.isin(res["shot"], pick)]
     _compare(sub, ref, 1e-4, allow_flip=1)
     assert (res["status"] >= 0).all()
