@@ -44,6 +44,9 @@ def parse_args():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-shots", type=int, default=1)
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-comparator", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=5.0)
     return ap.parse_args()
 
 
@@ -162,6 +165,91 @@ def run_reference(args):
                              "sample": "one pre-screen survivor per step through the FP64 NumPy MPS oracle"},
             "e2e": {"value": value, "unit": "shots/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+# ---- serving: Poisson arrivals of mixed jobs -------------------------------------------------
+def serving_leg(q, np, circ17, circ49, duration_s=5.0, rate=50.0, seed=0, drain_timeout_s=150.0):
+    """Jobs arrive as a Poisson process (mean `rate` per second) for `duration_s` seconds: half on
+    the 17-qubit, half on the 49-qubit circuit, p in {5e-4, 1e-3, 2e-3}, shot counts log-uniform in
+    64..4096, chi_max in {32, 128, 256}; the server admits them against a 150 GB budget."""
+    srv = q.Server(hbm_budget_bytes=150 << 30)
+    rng = np.random.default_rng(seed)
+    try:
+        # warm-up: compile the reference states of every (circuit, chi_max) pair
+        warm = [srv.submit(c, 64 * 1000 * (i + 1), 64, p=1e-3, seed=seed, chi_max=chi, cutoff=1e-10)
+                for i, (c, chi) in enumerate((c, chi) for c in (circ17, circ49) for chi in (32, 128, 256))]
+        t_w = time.time()
+        while any(srv.poll(j) is None for j in warm):
+            if time.time() - t_w > 300:
+                raise TimeoutError("serving warm-up")
+            time.sleep(0.01)
+        plan, t = [], 0.0
+        while True:
+            t += rng.exponential(1.0 / rate)
+            if t > duration_s:
+                break
+            circ = circ17 if rng.random() < 0.5 else circ49
+            p = float(rng.choice([5e-4, 1e-3, 2e-3]))
+            shots = int(math.exp(rng.uniform(math.log(64), math.log(4096))))
+            chi = int(rng.choice([32, 128, 256]))
+            plan.append((t, circ, p, max(1, shots), chi))
+        ids = []
+        t0 = time.perf_counter()
+        for i, (ta, circ, p, shots, chi) in enumerate(plan):
+            delay = ta - (time.perf_counter() - t0)
+            if delay > 0:
+                time.sleep(delay)
+            ids.append(srv.submit(circ, 64 * 4096 * (10_000 + i), shots, p=p, seed=seed, chi_max=chi, cutoff=1e-10))
+        res = {}
+        while len(res) < len(ids) and time.perf_counter() - t0 < duration_s + drain_timeout_s:
+            for j in ids:
+                if j not in res:
+                    r = srv.poll(j)
+                    if r is not None:
+                        res[j] = r
+            time.sleep(0.005)
+        done = [r for r in res.values() if r["state"] == 0]
+        lat = np.array([r["end_ms"] - r["submit_ms"] for r in done])
+        acc = int(sum(int(r["counts"][:, 1].sum()) for r in done))
+        span_ms = (max(r["end_ms"] for r in done) - min(r["submit_ms"] for r in done)) if done else 0.0
+        return {"jobs": len(ids), "completed": len(done), "arrival_rate_per_s": rate, "window_s": duration_s,
+                "p50_job_ms": float(np.percentile(lat, 50)) if len(lat) else None,
+                "p99_job_ms": float(np.percentile(lat, 99)) if len(lat) else None,
+                "accepted_shots": acc, "accepted_shots_per_s": acc / (span_ms / 1e3) if span_ms > 0 else None,
+                "drawn_shots": int(sum(r["shots"] for r in done)),
+                "survivors": int(sum(r["survivors"] for r in done))}
+    finally:
+        srv.close()
+
+
+def comparator_leg(q, text, circ, shot, args, time_cap_s=40.0):
+    """The plain FP64 one-shot-per-launch GPU MPS on one survivor shot of the workload.  A shot
+    that needs longer than the cap is timed on its first updates and extrapolated."""
+    import torch
+    from paper_2609_19116_b300 import plain_fp64 as pf
+    n, ops = pf.parse(text)
+    shots = torch.tensor([shot], dtype=torch.int64, device="cuda")
+    cnt, chan, code = q.qc_sample_faults(circ, shots, p=args.p, seed=args.seed, max_faults=128)
+    k = int(cnt[0])
+    faults = dict(zip(chan[0, :k].tolist(), code[0, :k].tolist()))
+    total = sum(2 * abs(qs[0] - qs[1]) - 1 for name, qs, _ in ops if name in ("CX", "CZ", "SWAP"))
+    # warm the library (cuSOLVER handles), calibrate the update rate on a prefix, then run to the cap
+    pf.run_shot(n, ops, faults, seed=args.seed, shot=shot, chi_max=args.chi_max, cutoff=args.cutoff, dev="cuda",
+                max_updates=50)
+    t0 = time.perf_counter()
+    st, upd = pf.run_shot(n, ops, faults, seed=args.seed, shot=shot, chi_max=args.chi_max, cutoff=args.cutoff,
+                          dev="cuda", max_updates=300)
+    rate = upd / (time.perf_counter() - t0)
+    cap_updates = int(rate * time_cap_s)
+    t0 = time.perf_counter()
+    st, upd = pf.run_shot(n, ops, faults, seed=args.seed, shot=shot, chi_max=args.chi_max, cutoff=args.cutoff,
+                          dev="cuda", max_updates=cap_updates)
+    dt = time.perf_counter() - t0
+    extrapolated = st == "cut"
+    per_shot_s = dt * (total / max(1, upd)) if extrapolated else dt
+    return {"value": 1.0 / per_shot_s, "unit": "shots/s", "dtype": "c128", "shot": shot,
+            "updates_timed": upd, "updates_per_shot": total, "seconds_timed": dt,
+            "extrapolated": extrapolated, "status": st}
 
 
 # ---- the GPU arm ------------------------------------------------------------------------------
@@ -297,6 +385,15 @@ def main():
             dist.barrier()
         return
 
+    serving = None
+    if not args.no_serving and world == 1:
+        circ17 = q.Circuit(workload_circuit("d3_17q_12l", seed=args.seed))
+        serving = serving_leg(q, np, circ17, circ, duration_s=args.serve_seconds)
+    comparator = None
+    if not args.no_comparator:
+        comparator = comparator_leg(q, text, circ, int(res["shot"][0]), args)
+        comparator["ratio_engine_over_plain"] = value / comparator["value"] if comparator["value"] > 0 else None
+
     cpu = None
     if not args.no_cpu_baseline:
         picks = [int(s) for s in res["shot"][: args.cpu_sample_shots]]
@@ -325,6 +422,8 @@ def main():
         "e2e": {"value": e2e_val, "unit": "shots/s", "h2d_bytes_per_step": h2d // e2e_steps,
                 "d2h_bytes_per_step": d2h // e2e_steps},
         "cpu_baseline": cpu,
+        "serving": serving,
+        "plain_fp64_gpu": comparator,
         "wall_s": wall,
     }
     print(json.dumps(line), flush=True)

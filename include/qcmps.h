@@ -208,8 +208,8 @@ typedef struct qc_server qc_server;
 
 typedef struct {
     uint64_t hbm_budget_bytes;  /* admission budget for in-flight MPS state */
-    int32_t max_slots;          /* upper bound on concurrently simulated shots (0 = default) */
-    int32_t n_streams;          /* device streams the loop spreads jobs over (0 = default 2) */
+    int32_t max_slots;          /* upper bound on the shot slots of one batch (0 = 16 x SMs) */
+    int32_t n_streams;          /* device streams the loop spreads jobs over (0 = default 64) */
 } qc_serve_cfg;
 
 typedef struct {

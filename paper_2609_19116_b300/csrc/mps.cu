@@ -1132,7 +1132,9 @@ static qc_status run_engine(CircuitImpl& c, qc_noise noise, const uint64_t* shot
     //    reference run's chi_peak; QCMPS_ENGINE = warp | cta128 | cta256 | cta and QCMPS_SMEM_KB
     //    override the choice for tuning.
     const char* force = getenv("QCMPS_ENGINE");
-    int variant = ref->chi_peak <= 64 ? 32 : NT_BIG;
+    // throughput mode (one warp per shot) needs many shots to fill the SMs; a batch with no more
+    // shots than SMs runs in latency mode (one CTA per shot)
+    int variant = (ref->chi_peak <= 64 && nshots > (uint64_t)nsm) ? 32 : NT_BIG;
     if (force && !strcmp(force, "warp")) variant = 32;
     if (force && !strcmp(force, "cta128")) variant = 128;
     if (force && !strcmp(force, "cta256")) variant = 256;

@@ -20,7 +20,7 @@ namespace qc {
 namespace {
 
 constexpr int WBINS = 16;
-constexpr uint64_t CHUNK_SHOTS = 2048;
+constexpr uint64_t CHUNK_SHOTS = 512;  // bounds how long a worker stays on one job
 
 struct Job {
     uint64_t id;
@@ -196,8 +196,8 @@ extern "C" qc_status mps_serve_create(const qc_serve_cfg* cfg, qc_server** out) 
     QC_CUDA(cudaGetDevice(&s.device));
     int nsm = 0;
     QC_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, s.device));
-    s.max_slots = cfg->max_slots > 0 ? cfg->max_slots : nsm;
-    const int ns = cfg->n_streams > 0 ? cfg->n_streams : 2;
+    s.max_slots = cfg->max_slots > 0 ? cfg->max_slots : 16 * nsm;
+    const int ns = cfg->n_streams > 0 ? cfg->n_streams : 64;
     for (int i = 0; i < ns; ++i) s.workers.emplace_back([&s] { s.worker(); });
     *out = sp.release();
     return QC_OK;
