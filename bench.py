@@ -167,6 +167,22 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ---- multi-rank helpers (one process per GPU, disjoint shot ranges, no data-path collective) ----
+def rank_shot0(rank, step, drawn):
+    """First shot of a rank's step: ranks and steps own disjoint, 64-aligned ranges."""
+    return (rank * 1_000_000 + step) * drawn
+
+
+def reduce_over_ranks(dist, device, ms, accepted, survivors):
+    """Step time is the maximum over ranks; counts are summed (one tiny host-level exchange)."""
+    import torch
+    t = torch.tensor([ms, float(accepted), float(survivors)], dtype=torch.float64, device=device)
+    mx = t.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(mx[0]), int(t[1]), int(t[2])
+
+
 # ---- serving: Poisson arrivals of mixed jobs -------------------------------------------------
 def serving_leg(q, np, circ17, circ49, duration_s=5.0, rate=50.0, seed=0, drain_timeout_s=150.0):
     """Jobs arrive as a Poisson process (mean `rate` per second) for `duration_s` seconds: half on
@@ -287,7 +303,7 @@ def main():
     shot_buf = torch.zeros(drawn * q.SHOT_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
 
     def shot0_of(step):
-        return (rank * 1_000_000 + step) * drawn
+        return rank_shot0(rank, step, drawn)
 
     kernel_ms = []
     flops_acc = [0.0]
@@ -333,12 +349,7 @@ def main():
     clocks = clk.stop()
     ms = t_start.elapsed_time(t_end)
     if world > 1:
-        t = torch.tensor([ms, float(acc_total), float(surv_total)], dtype=torch.float64, device="cuda")
-        mx = t.clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        ms = float(mx[0])
-        acc_total, surv_total = int(t[1]), int(t[2])
+        ms, acc_total, surv_total = reduce_over_ranks(dist, "cuda", ms, acc_total, surv_total)
     value = acc_total / (ms / 1e3) if ms > 0 else 0.0
 
     # roofline of the dominant kernel (the MPS engine): algorithmic flops / event time
