@@ -187,13 +187,16 @@ def reduce_over_ranks(dist, device, ms, accepted, survivors):
 def serving_leg(q, np, circ17, circ49, duration_s=5.0, rate=50.0, seed=0, drain_timeout_s=150.0):
     """Jobs arrive as a Poisson process (mean `rate` per second) for `duration_s` seconds: half on
     the 17-qubit, half on the 49-qubit circuit, p in {5e-4, 1e-3, 2e-3}, shot counts log-uniform in
-    64..4096, chi_max in {32, 128, 256}; the server admits them against a 150 GB budget."""
+    64..4096, chi_max in {32, 128, 256} (32 only with the 17-qubit circuit: it is below the 49-qubit
+    circuit's chi_peak of 64, where the truncated noiseless reference is not deterministic); the
+    server admits them against a 150 GB budget."""
     srv = q.Server(hbm_budget_bytes=150 << 30)
     rng = np.random.default_rng(seed)
     try:
         # warm-up: compile the reference states of every (circuit, chi_max) pair
+        pairs = [(circ17, 32), (circ17, 128), (circ17, 256), (circ49, 128), (circ49, 256)]
         warm = [srv.submit(c, 64 * 1000 * (i + 1), 64, p=1e-3, seed=seed, chi_max=chi, cutoff=1e-10)
-                for i, (c, chi) in enumerate((c, chi) for c in (circ17, circ49) for chi in (32, 128, 256))]
+                for i, (c, chi) in enumerate(pairs)]
         t_w = time.time()
         while any(srv.poll(j) is None for j in warm):
             if time.time() - t_w > 300:
@@ -207,7 +210,7 @@ def serving_leg(q, np, circ17, circ49, duration_s=5.0, rate=50.0, seed=0, drain_
             circ = circ17 if rng.random() < 0.5 else circ49
             p = float(rng.choice([5e-4, 1e-3, 2e-3]))
             shots = int(math.exp(rng.uniform(math.log(64), math.log(4096))))
-            chi = int(rng.choice([32, 128, 256]))
+            chi = int(rng.choice([32, 128, 256] if circ is circ17 else [128, 256]))
             plan.append((t, circ, p, max(1, shots), chi))
         ids = []
         t0 = time.perf_counter()
@@ -228,7 +231,8 @@ def serving_leg(q, np, circ17, circ49, duration_s=5.0, rate=50.0, seed=0, drain_
         lat = np.array([r["end_ms"] - r["submit_ms"] for r in done])
         acc = int(sum(int(r["counts"][:, 1].sum()) for r in done))
         span_ms = (max(r["end_ms"] for r in done) - min(r["submit_ms"] for r in done)) if done else 0.0
-        return {"jobs": len(ids), "completed": len(done), "arrival_rate_per_s": rate, "window_s": duration_s,
+        return {"jobs": len(ids), "completed": len(done), "failed": sum(1 for r in res.values() if r["state"] != 0),
+                "arrival_rate_per_s": rate, "window_s": duration_s,
                 "p50_job_ms": float(np.percentile(lat, 50)) if len(lat) else None,
                 "p99_job_ms": float(np.percentile(lat, 99)) if len(lat) else None,
                 "accepted_shots": acc, "accepted_shots_per_s": acc / (span_ms / 1e3) if span_ms > 0 else None,

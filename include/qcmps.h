@@ -120,7 +120,8 @@ typedef struct {
  *   survivors      optional (NULL): surviving shot indices, increasing
  *   hist_drawn, hist_kept  optional host arrays of w_max+1 counts: shots per fault weight w
  *                  (bin w_max collects w >= w_max), all drawn / surviving
- * Bernoulli noise only (fault_weight = -1).  Synchronises `stream` before returning. */
+ * Bernoulli noise (fault_weight = -1), or a fixed weight 0..32 (subset sampling, Sec. 4.1; up to
+ * 128 qubits).  Synchronises `stream` before returning. */
 qc_status pauli_prescreen(const qc_circuit* circuit, qc_noise noise, uint64_t shot0,
                           uint64_t nshots, uint64_t* kept_mask_dev, qc_survivors* survivors,
                           uint64_t* hist_drawn, uint64_t* hist_kept, int32_t w_max, void* stream);

@@ -87,7 +87,7 @@ def qc_sample_faults(circ: Circuit, shots: torch.Tensor, *, p: float, seed: int,
 
 def pauli_prescreen(circ: Circuit, shot0: int, nshots: int, *, p: float, seed: int, w_max: int = 15,
                     survivors_capacity: int | None = None, kept_mask: torch.Tensor | None = None,
-                    survivors: torch.Tensor | None = None, device=None, stream=None):
+                    survivors: torch.Tensor | None = None, fault_weight: int = -1, device=None, stream=None):
     """Returns dict(kept_mask (int64 words), survivors (int64, first n), n_kept, hist_drawn, hist_kept)."""
     device = device or torch.device("cuda")
     nwords = (nshots + 63) // 64
@@ -101,7 +101,7 @@ def pauli_prescreen(circ: Circuit, shot0: int, nshots: int, *, p: float, seed: i
                        survivors.numel() if survivors is not None else 0, 0)
     hd = np.zeros(w_max + 1, dtype=np.uint64)
     hk = np.zeros(w_max + 1, dtype=np.uint64)
-    N.check(N.lib().pauli_prescreen(circ.handle, N.Noise(p, seed, -1), shot0, nshots, _ptr(kept_mask),
+    N.check(N.lib().pauli_prescreen(circ.handle, N.Noise(p, seed, fault_weight), shot0, nshots, _ptr(kept_mask),
                                     C.byref(surv), hd.ctypes.data_as(C.c_void_p), hk.ctypes.data_as(C.c_void_p),
                                     w_max, _stream(stream)))
     n = surv.count

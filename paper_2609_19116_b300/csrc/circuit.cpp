@@ -349,6 +349,11 @@ CircuitImpl::~CircuitImpl() {
         cudaFree(kv.second.dims);
         cudaFree(kv.second.cap);
         cudaFree(kv.second.off);
+        for (auto& pk : kv.second.packed) {
+            cudaFree(pk.second.state);
+            cudaFree(pk.second.cap);
+            cudaFree(pk.second.off);
+        }
         cudaSetDevice(cur);
     }
 }

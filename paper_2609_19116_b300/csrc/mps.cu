@@ -65,13 +65,18 @@ struct EngineParams {
     uint64_t xg_elems;    // size of the X part of a slot's scratch
     uint32_t x_smem;      // capacity (elements) of the shared-memory X
     uint32_t x_big;       // warp mode: capacity (elements) of the CTA's shared large work area
-    int chi_max;
+    int chi_max;          // capacity of every bond in this launch's slot layout
+    int chi_trunc;        // the truncation cap (the caller's chi_max, at most the exact bound)
+    int defer_capacity;   // 1: a shot that outgrows the capacity is reported but not counted
+    int shared_gpu;       // 1: other batches run concurrently (serving): prefer throughput mode
     double cutoff;
     uint32_t k0, k1;
     uint32_t tg[64];
     int32_t weight;
     int reference;        // 1: noiseless reference run writing into `mps` slot 0
-    const V* ref;         // reference state (same layout as one slot)
+    const V* ref;         // reference state
+    const uint64_t* ref_off;  // site offsets of the reference state [nq+1]
+    int ref_chi;              // largest bond of the reference state
     const int* ref_dims;  // [nq+1]
     double ref_disc;
     double ref_norm;
@@ -454,7 +459,7 @@ struct Engine {
                 tail += (double)sig2[perm[r - 1]];
                 --r;
             }
-            while (r > P.chi_max || (r > 1 && r > nz)) {
+            while (r > P.chi_trunc || (r > 1 && r > nz)) {
                 tail += (double)sig2[perm[r - 1]];
                 --r;
             }
@@ -603,7 +608,7 @@ struct Engine {
     // ---- <ref|psi> by a transfer sweep ----------------------------------------------------------
     __device__ double2 overlap_ref() {
         // E: (chi_ref x chi), T1: (chi_ref x 2 x chi); placed in shared X when it fits
-        const int cap2 = P.chi_max;  // upper bound of any bond
+        const int cap2 = max(P.chi_max, P.ref_chi);  // bounds the bonds of both states
         const uint64_t need = (uint64_t)cap2 * cap2 * 3;
         V* E = (need <= P.x_smem) ? S.X : xg;
         V* T1 = E + (size_t)cap2 * cap2;
@@ -614,7 +619,7 @@ struct Engine {
             const int ca = P.ref_dims[q], ca2 = P.ref_dims[q + 1];
             const int cb = S.dims[q], cb2 = S.dims[q + 1];
             const V* Aq = site(q);
-            const V* Rq = refsite + P.off[q];
+            const V* Rq = refsite + P.ref_off[q];
             // T1[a][s][b'] = sum_b E[a][b] A[b][s][b']
             for (int e = tid_; e < ca * 2 * cb2; e += NT) {
                 const int a_ = e / (2 * cb2), rest = e - a_ * 2 * cb2;
@@ -791,13 +796,15 @@ struct Engine {
                 *P.ref_disc_out = disc;
                 *P.ref_chi_out = chi_peak;
                 if (status != 0) atomicCAS(P.ref_status, 0, -1000 + status);
-            } else {
+            } else if (!(P.defer_capacity && status == QC_ECAPACITY)) {
                 const int wb = min(nf, P.wmax);
                 atomicAdd(&P.counts[3 * wb + 0], 1ull);
                 if (status == 0) {
                     atomicAdd(&P.counts[3 * wb + 1], 1ull);
                     if (lerr) atomicAdd(&P.counts[3 * wb + 2], 1ull);
                 }
+            }
+            if (!P.reference) {
                 if (P.per_shot) {
                     qc_shot_result res;
                     res.shot = shot;
@@ -992,6 +999,118 @@ static size_t configure_smem(EngineParams<R>& P, size_t budget, uint64_t x_full)
     return engine_smem<R, NT>(P);
 }
 
+// One persistent launch over `nshots` shots with slots of layout L (reference stored in L).
+template <typename R, int NT_BIG>
+static qc_status run_pass(CircuitImpl& c, EngineParams<R> P, const SlotLayout& L, const void* ref_state,
+                          const int* cap_dev, const uint64_t* off_dev, const RefState& ref,
+                          const uint64_t* shots_dev, uint64_t nshots, unsigned long long* counts_dev,
+                          qc_shot_result* per_shot, cudaStream_t s, int max_slots, int nsm, bool defer) {
+    using V = typename VecOf<R>::T;
+    const int chi = P.chi_max;
+    P.ref_chi = std::max(1, ref.chi_peak);
+    const uint64_t cap2 = (uint64_t)std::max(chi, P.ref_chi);
+    const uint64_t x_full = (uint64_t)(2 * chi + 1) * (2 * chi);
+    const uint64_t over_full = cap2 * cap2 * 3;
+    const uint64_t xg_elems = std::max(x_full, over_full);
+    const uint64_t sg_elems = ((uint64_t)(2 * chi) * (sizeof(R) + sizeof(int)) + sizeof(V) - 1) / sizeof(V) + 2;
+    const uint64_t scratch_stride = xg_elems + (uint64_t)(2 * chi) * (2 * chi) + sg_elems;
+    P.slot_stride = L.stride;
+    P.scratch_stride = scratch_stride;
+    P.xg_elems = xg_elems;
+    P.defer_capacity = defer ? 1 : 0;
+    // the variant (threads per shot, shared-memory budget per shot) follows the reference run's
+    // chi_peak and the batch size; QCMPS_ENGINE = warp | cta128 | cta256 | cta and QCMPS_SMEM_KB,
+    // QCMPS_WARPS, QCMPS_BIG_KB override it for tuning.
+    const char* force = getenv("QCMPS_ENGINE");
+    // throughput mode (one warp per shot) needs many shots to fill the SMs; a batch with no more
+    // shots than SMs runs in latency mode (one CTA per shot) unless the caller shares the GPU with
+    // other batches (the serving loop), where throughput mode keeps more shots in flight
+    int variant = (ref.chi_peak <= 64 && (nshots > (uint64_t)nsm || P.shared_gpu)) ? 32 : NT_BIG;
+    if (force && !strcmp(force, "warp")) variant = 32;
+    if (force && !strcmp(force, "cta128")) variant = 128;
+    if (force && !strcmp(force, "cta256")) variant = 256;
+    if (force && !strcmp(force, "cta")) variant = NT_BIG;
+    const char* kb = getenv("QCMPS_SMEM_KB");
+    const int kbv = kb ? atoi(kb) : 0;
+    const char* wv = getenv("QCMPS_WARPS");
+    const char* bv = getenv("QCMPS_BIG_KB");
+    size_t smem;
+    int nt = variant;
+    int engines = 1;  // engines (shot slots) per CTA
+    const void* fn;
+    if (variant == 32) {
+        // measured on the 49-qubit workload: one warp per CTA with 24 KB (9 shot slots per SM)
+        // beats sharing a large area between warps (contention) and larger per-warp areas (fewer
+        // slots)
+        engines = (wv && atoi(wv) >= 1 && atoi(wv) <= 8) ? atoi(wv) : 1;
+        const size_t per = configure_smem<R, 32>(P, (kbv >= 8 && kbv <= 200 ? kbv : 24) * 1024, xg_elems);
+        const size_t region = (per + 15) & ~(size_t)15;
+        const size_t big_budget = (bv && atoi(bv) >= 0) ? (size_t)atoi(bv) * 1024 : 0;
+        size_t room = 227 * 1024 > region * engines + 16 ? 227 * 1024 - region * engines - 16 : 0;
+        if (engines == 1) room = 0;  // nobody to share with
+        room = std::min(room, big_budget);
+        P.x_big = (uint32_t)std::min<uint64_t>((room / sizeof(V)) & ~1ull, 4 * xg_elems);
+        smem = region * engines + (size_t)P.x_big * sizeof(V) + 16;
+        fn = (const void*)engine_kernel<R, 32>;
+        nt = 32 * engines;
+    } else if (variant == 128) {
+        smem = configure_smem<R, 128>(P, (kbv >= 8 && kbv <= 200 ? kbv : 72) * 1024, xg_elems);
+        fn = (const void*)engine_kernel<R, 128>;
+    } else if (variant == 256) {
+        smem = configure_smem<R, 256>(P, (kbv >= 8 && kbv <= 200 ? kbv : 100) * 1024, xg_elems);
+        fn = (const void*)engine_kernel<R, 256>;
+    } else {
+        smem = configure_smem<R, NT_BIG>(P, 200 * 1024, xg_elems);
+        fn = (const void*)engine_kernel<R, NT_BIG>;
+        nt = NT_BIG;
+    }
+    QC_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    QC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, nt, smem));
+    if (per_sm < 1) return fail(QC_ENOMEM, "engine does not fit on an SM (smem %zu)", smem);
+    uint64_t ctas = std::min<uint64_t>((nshots + engines - 1) / engines, (uint64_t)per_sm * nsm);
+    if (max_slots > 0) ctas = std::min<uint64_t>(ctas, std::max<uint64_t>(1, (uint64_t)max_slots / engines));
+    if (ctas < 1) ctas = 1;
+    const uint64_t slots = ctas * engines;
+
+    const uint64_t mps_elems = slots * L.stride;
+    const uint64_t scr_elems = slots * scratch_stride;
+    char* ws = nullptr;
+    const size_t bytes = (mps_elems + scr_elems) * sizeof(V) + 64;
+    cudaError_t e = cudaMallocAsync((void**)&ws, bytes, s);
+    if (e != cudaSuccess) return fail(QC_ENOMEM, "workspace of %zu bytes: %s", bytes, cudaGetErrorString(e));
+    qc_status out = QC_OK;
+    do {
+        V* mps = reinterpret_cast<V*>(ws + 64);
+        V* scr = mps + mps_elems;
+        e = cudaMemsetAsync(ws, 0, 64, s);
+        if (e != cudaSuccess) { out = cuda_fail(e, "workspace init"); break; }
+        P.reference = 0;
+        P.mps = mps;
+        P.off = off_dev;
+        P.cap = cap_dev;
+        P.scratch = scr;
+        P.ref = reinterpret_cast<const V*>(ref_state);
+        P.ref_off = ref.off;
+        P.ref_dims = ref.dims;
+        P.ref_disc = ref.disc;
+        P.ref_norm = ref.norm;
+        P.shots = shots_dev;
+        P.ntasks = nshots;
+        P.next_task = reinterpret_cast<unsigned long long*>(ws);
+        P.per_shot = per_shot;
+        P.counts = counts_dev;
+        if (variant == 32) engine_kernel<R, 32><<<(unsigned)ctas, 32 * engines, smem, s>>>(P);
+        else if (variant == 128) engine_kernel<R, 128><<<(unsigned)ctas, 128, smem, s>>>(P);
+        else if (variant == 256) engine_kernel<R, 256><<<(unsigned)ctas, 256, smem, s>>>(P);
+        else engine_kernel<R, NT_BIG><<<(unsigned)ctas, NT_BIG, smem, s>>>(P);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) { out = cuda_fail(e, "engine"); break; }
+    } while (0);
+    cudaFreeAsync(ws, s);
+    return out;
+}
+
 // Host driver shared by mps_sample_batch and the serving loop.
 //
 // chi-bucketed variants: the reference run tells the bond dimensions the circuit reaches.  When
@@ -1001,7 +1120,7 @@ static size_t configure_smem(EngineParams<R>& P, size_t budget, uint64_t x_full)
 template <typename R, int NT_BIG>
 static qc_status run_engine(CircuitImpl& c, qc_noise noise, const uint64_t* shots_dev, uint64_t nshots,
                             qc_mps_params prm, unsigned long long* counts_dev, int wmax,
-                            qc_shot_result* per_shot, cudaStream_t s, int max_slots) {
+                            qc_shot_result* per_shot, cudaStream_t s, int max_slots, bool shared_gpu) {
     using V = typename VecOf<R>::T;
     DeviceCopy* dc;
     qc_status st = c.device_copy(&dc);
@@ -1023,6 +1142,8 @@ static qc_status run_engine(CircuitImpl& c, qc_noise noise, const uint64_t* shot
 
     EngineParams<R> P{};
     P.chi_max = chi;
+    P.chi_trunc = chi;
+    P.shared_gpu = shared_gpu ? 1 : 0;
     P.prog = dc->mps;
     P.nops = (uint32_t)c.mps.size();
     P.nq = c.n;
@@ -1080,6 +1201,8 @@ static qc_status run_engine(CircuitImpl& c, qc_noise noise, const uint64_t* shot
                 Pr.reference = 1;
                 Pr.mps = reinterpret_cast<V*>(rs.state);
                 Pr.off = rs.off;
+                Pr.ref_off = rs.off;
+                Pr.ref_chi = chi;
                 Pr.cap = rs.cap;
                 Pr.scratch = reinterpret_cast<V*>(tmp + 64);
                 Pr.ntasks = 1;
@@ -1128,102 +1251,83 @@ static qc_status run_engine(CircuitImpl& c, qc_noise noise, const uint64_t* shot
     }
     if (nshots == 0) return QC_OK;
 
-    // 2. the shots: the variant (threads per shot, shared-memory budget per shot) follows the
-    //    reference run's chi_peak; QCMPS_ENGINE = warp | cta128 | cta256 | cta and QCMPS_SMEM_KB
-    //    override the choice for tuning.
-    const char* force = getenv("QCMPS_ENGINE");
-    // throughput mode (one warp per shot) needs many shots to fill the SMs; a batch with no more
-    // shots than SMs runs in latency mode (one CTA per shot)
-    int variant = (ref->chi_peak <= 64 && nshots > (uint64_t)nsm) ? 32 : NT_BIG;
-    if (force && !strcmp(force, "warp")) variant = 32;
-    if (force && !strcmp(force, "cta128")) variant = 128;
-    if (force && !strcmp(force, "cta256")) variant = 256;
-    if (force && !strcmp(force, "cta")) variant = NT_BIG;
-    const char* kb = getenv("QCMPS_SMEM_KB");
-    const int kbv = kb ? atoi(kb) : 0;
-    const char* wv = getenv("QCMPS_WARPS");
-    const char* bv = getenv("QCMPS_BIG_KB");
-    size_t smem;
-    int nt = variant;
-    int engines = 1;  // engines (shot slots) per CTA
-    const void* fn;
-    const uint64_t xf = std::max(x_full, over_full);
-    if (variant == 32) {
-        // warp mode: `engines` warps per CTA, each with its own work area, plus one shared large area
-        // measured on the 49-qubit workload: one warp per CTA with 24 KB (9 shot slots per SM)
-        // beats sharing a large area between warps (contention) and larger per-warp areas (fewer
-        // slots)
-        engines = (wv && atoi(wv) >= 1 && atoi(wv) <= 8) ? atoi(wv) : 1;
-        const size_t per = configure_smem<R, 32>(P, (kbv >= 8 && kbv <= 200 ? kbv : 24) * 1024, xf);
-        const size_t region = (per + 15) & ~(size_t)15;
-        const size_t big_budget = (bv && atoi(bv) >= 0) ? (size_t)atoi(bv) * 1024 : 0;
-        size_t room = 227 * 1024 > region * engines + 16 ? 227 * 1024 - region * engines - 16 : 0;
-        if (engines == 1) room = 0;  // nobody to share with
-        room = std::min(room, big_budget);
-        P.x_big = (uint32_t)std::min<uint64_t>((room / sizeof(V)) & ~1ull, 4 * xf);
-        smem = region * engines + (size_t)P.x_big * sizeof(V) + 16;
-        fn = (const void*)engine_kernel<R, 32>;
-        nt = 32 * engines;
-    } else if (variant == 128) {
-        smem = configure_smem<R, 128>(P, (kbv >= 8 && kbv <= 200 ? kbv : 72) * 1024, xf);
-        fn = (const void*)engine_kernel<R, 128>;
-    } else if (variant == 256) {
-        smem = configure_smem<R, 256>(P, (kbv >= 8 && kbv <= 200 ? kbv : 100) * 1024, xf);
-        fn = (const void*)engine_kernel<R, 256>;
-    } else {
-        smem = configure_smem<R, NT_BIG>(P, 200 * 1024, xf);
-        fn = (const void*)engine_kernel<R, NT_BIG>;
-        nt = NT_BIG;
+    // 2. capacity bucket: slots sized for chi_alloc = min(chi, max(64, 2 chi_peak_ref)); a shot
+    //    that outgrows it is reported by the first pass and re-run with full capacity
+    int chi_alloc = 64;
+    while (chi_alloc < 2 * ref->chi_peak) chi_alloc *= 2;
+    chi_alloc = std::min(chi_alloc, chi);
+    if (const char* ca = getenv("QCMPS_CHI_ALLOC")) chi_alloc = std::max(1, std::min(chi, atoi(ca)));
+    if (chi_alloc >= chi)
+        return run_pass<R, NT_BIG>(c, P, L, ref->state, ref->cap, ref->off, *ref, shots_dev, nshots, counts_dev,
+                                   per_shot, s, max_slots, nsm, false);
+    const SlotLayout L1 = slot_layout(c.n, chi_alloc);
+    int* cap1 = nullptr;
+    uint64_t* off1 = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(c.ref_mu);
+        auto it = ref->packed.find(chi_alloc);
+        if (it == ref->packed.end()) {
+            RefPacked rp;  // the bucket's slot layout (the reference keeps its own)
+            cudaError_t e = cudaMalloc(&rp.cap, (c.n + 1) * sizeof(int));
+            if (e == cudaSuccess) e = cudaMalloc(&rp.off, (c.n + 1) * sizeof(uint64_t));
+            if (e == cudaSuccess) e = cudaMemcpy(rp.cap, L1.cap.data(), (c.n + 1) * sizeof(int), cudaMemcpyHostToDevice);
+            if (e == cudaSuccess) e = cudaMemcpy(rp.off, L1.off.data(), (c.n + 1) * sizeof(uint64_t), cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) {
+                cudaFree(rp.cap); cudaFree(rp.off);
+                return cuda_fail(e, "bucket layout");
+            }
+            it = ref->packed.emplace(chi_alloc, rp).first;
+        }
+        cap1 = it->second.cap;
+        off1 = it->second.off;
     }
-    QC_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int per_sm = 0;
-    QC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, nt, smem));
-    if (per_sm < 1) return fail(QC_ENOMEM, "engine does not fit on an SM (smem %zu)", smem);
-    uint64_t ctas = std::min<uint64_t>((nshots + engines - 1) / engines, (uint64_t)per_sm * nsm);
-    if (max_slots > 0) ctas = std::min<uint64_t>(ctas, std::max<uint64_t>(1, (uint64_t)max_slots / engines));
-    if (ctas < 1) ctas = 1;
-    const uint64_t slots = ctas * engines;
-
-    const uint64_t mps_elems = slots * L.stride;
-    const uint64_t scr_elems = slots * scratch_stride;
-    char* ws = nullptr;
-    const size_t bytes = (mps_elems + scr_elems) * sizeof(V) + 64;
-    cudaError_t e = cudaMallocAsync((void**)&ws, bytes, s);
-    if (e != cudaSuccess) return fail(QC_ENOMEM, "workspace of %zu bytes: %s", bytes, cudaGetErrorString(e));
-    qc_status out = QC_OK;
-    do {
-        V* mps = reinterpret_cast<V*>(ws + 64);
-        V* scr = mps + mps_elems;
-        e = cudaMemsetAsync(ws, 0, 64, s);
-        if (e != cudaSuccess) { out = cuda_fail(e, "workspace init"); break; }
-        P.reference = 0;
-        P.mps = mps;
-        P.off = ref->off;
-        P.cap = ref->cap;
-        P.scratch = scr;
-        P.ref = reinterpret_cast<const V*>(ref->state);
-        P.ref_dims = ref->dims;
-        P.ref_disc = ref->disc;
-        P.ref_norm = ref->norm;
-        P.shots = shots_dev;
-        P.ntasks = nshots;
-        P.next_task = reinterpret_cast<unsigned long long*>(ws);
-        P.per_shot = per_shot;
-        P.counts = counts_dev;
-        if (variant == 32) engine_kernel<R, 32><<<(unsigned)ctas, 32 * engines, smem, s>>>(P);
-        else if (variant == 128) engine_kernel<R, 128><<<(unsigned)ctas, 128, smem, s>>>(P);
-        else if (variant == 256) engine_kernel<R, 256><<<(unsigned)ctas, 256, smem, s>>>(P);
-        else engine_kernel<R, NT_BIG><<<(unsigned)ctas, NT_BIG, smem, s>>>(P);
-        e = cudaGetLastError();
-        if (e != cudaSuccess) { out = cuda_fail(e, "engine"); break; }
-    } while (0);
-    cudaFreeAsync(ws, s);
+    // first pass: per-shot results are needed to find the shots that outgrew the bucket
+    qc_shot_result* res1 = per_shot;
+    if (!res1) QC_CUDA(cudaMallocAsync((void**)&res1, nshots * sizeof(qc_shot_result), s));
+    EngineParams<R> P1 = P;
+    P1.chi_max = chi_alloc;
+    qc_status out = run_pass<R, NT_BIG>(c, P1, L1, ref->state, cap1, off1, *ref, shots_dev, nshots, counts_dev, res1,
+                                        s, max_slots, nsm, true);
+    std::vector<qc_shot_result> h;
+    if (out == QC_OK) {
+        h.resize(nshots);
+        cudaError_t e = cudaMemcpyAsync(h.data(), res1, nshots * sizeof(qc_shot_result), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) out = cuda_fail(e, "first pass");
+    }
+    std::vector<uint64_t> redo, where;
+    for (uint64_t i = 0; out == QC_OK && i < nshots; ++i)
+        if (h[i].status == QC_ECAPACITY) { redo.push_back(h[i].shot); where.push_back(i); }
+    if (out == QC_OK && !redo.empty()) {
+        // second pass with the full capacity, then the records go back to their places
+        uint64_t* shots2 = nullptr;
+        qc_shot_result* res2 = nullptr;
+        cudaError_t e = cudaMallocAsync((void**)&shots2, redo.size() * sizeof(uint64_t), s);
+        if (e == cudaSuccess) e = cudaMallocAsync((void**)&res2, redo.size() * sizeof(qc_shot_result), s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(shots2, redo.data(), redo.size() * sizeof(uint64_t), cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) out = cuda_fail(e, "second pass");
+        if (out == QC_OK)
+            out = run_pass<R, NT_BIG>(c, P, L, ref->state, ref->cap, ref->off, *ref, shots2, redo.size(), counts_dev,
+                                      res2, s, max_slots, nsm, false);
+        if (out == QC_OK && per_shot) {
+            std::vector<qc_shot_result> h2(redo.size());
+            e = cudaMemcpyAsync(h2.data(), res2, h2.size() * sizeof(qc_shot_result), cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            for (size_t k = 0; e == cudaSuccess && k < where.size(); ++k)
+                e = cudaMemcpyAsync(per_shot + where[k], &h2[k], sizeof(qc_shot_result), cudaMemcpyHostToDevice, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) out = cuda_fail(e, "second pass results");
+        }
+        cudaFreeAsync(shots2, s);
+        cudaFreeAsync(res2, s);
+    }
+    if (res1 != per_shot) cudaFreeAsync(res1, s);
     return out;
 }
 
 qc_status engine_launch(CircuitImpl& c, qc_noise noise, const uint64_t* shots_dev, uint64_t nshots,
                         qc_mps_params prm, unsigned long long* counts_dev, int wmax, qc_shot_result* per_shot,
-                        cudaStream_t s, int max_slots) {
+                        cudaStream_t s, int max_slots, bool shared_gpu) {
     if (!(noise.p >= 0.0 && noise.p < 1.0)) return fail(QC_EINVAL, "p must lie in [0, 1)");
     if (prm.chi_max < 1) return fail(QC_EINVAL, "chi_max must be >= 1");
     if (!(prm.cutoff >= 0.0)) return fail(QC_EINVAL, "cutoff must be >= 0");
@@ -1234,8 +1338,10 @@ qc_status engine_launch(CircuitImpl& c, qc_noise noise, const uint64_t* shots_de
     if (nshots && !shots_dev) return fail(QC_EINVAL, "null shots");
     if (c.n < 2) return fail(QC_EINVAL, "the MPS engine needs at least two qubits");
     if (prm.precision == QC_C64)
-        return run_engine<float, NT_F>(c, noise, shots_dev, nshots, prm, counts_dev, wmax, per_shot, s, max_slots);
-    return run_engine<double, NT_D>(c, noise, shots_dev, nshots, prm, counts_dev, wmax, per_shot, s, max_slots);
+        return run_engine<float, NT_F>(c, noise, shots_dev, nshots, prm, counts_dev, wmax, per_shot, s, max_slots,
+                                       shared_gpu);
+    return run_engine<double, NT_D>(c, noise, shots_dev, nshots, prm, counts_dev, wmax, per_shot, s, max_slots,
+                                    shared_gpu);
 }
 
 qc_status shot_footprint(const CircuitImpl& c, qc_mps_params prm, uint64_t* bytes) {
@@ -1265,7 +1371,7 @@ extern "C" qc_status mps_sample_batch(const qc_circuit* circuit, qc_noise noise,
     qc_status st = QC_OK;
     cudaError_t e = cudaMemsetAsync(counts, 0, cb, s);
     if (e != cudaSuccess) st = cuda_fail(e, "memset");
-    if (st == QC_OK) st = engine_launch(c, noise, shots_dev, nshots, params, counts, w_max, per_shot_dev, s, 0);
+    if (st == QC_OK) st = engine_launch(c, noise, shots_dev, nshots, params, counts, w_max, per_shot_dev, s, 0, false);
     if (st == QC_OK) {
         std::vector<unsigned long long> h(3 * (w_max + 1));
         e = cudaMemcpyAsync(h.data(), counts, cb, cudaMemcpyDeviceToHost, s);

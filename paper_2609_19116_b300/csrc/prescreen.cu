@@ -185,6 +185,103 @@ __global__ void __launch_bounds__(PRE_THREADS) prescreen_kernel(const PreParams 
     }
 }
 
+// ---- fixed-weight pre-screen (subset sampling, Sec. 4.1): one thread per shot --------------------
+// Each shot has exactly w faults (Floyd's algorithm over the channels); the thread keeps them sorted
+// by channel and sweeps the frame program with the frame in registers (x and z bits of up to 128
+// qubits), so a noise instruction only compares its channel with the next fault.
+constexpr int EX_MAXW = 32;
+constexpr int EX_THREADS = 128;
+
+__device__ __forceinline__ bool bit2(const uint64_t (&v)[2], uint32_t q) { return (v[q >> 6] >> (q & 63)) & 1; }
+__device__ __forceinline__ void flip2(uint64_t (&v)[2], uint32_t q, bool b) { v[q >> 6] ^= (uint64_t)b << (q & 63); }
+__device__ __forceinline__ void clr2(uint64_t (&v)[2], uint32_t q) { v[q >> 6] &= ~(1ull << (q & 63)); }
+
+__global__ void __launch_bounds__(EX_THREADS) prescreen_exact_kernel(const PreParams P, int weight) {
+    __shared__ PreOp chunk[PRE_CHUNK];
+    __shared__ unsigned long long hd, hk;
+    const uint64_t i = (uint64_t)blockIdx.x * EX_THREADS + threadIdx.x;
+    const bool active = i < P.nshots;
+    const uint64_t shot = P.word0 * 64 + i;
+    if (threadIdx.x == 0) { hd = 0; hk = 0; }
+    uint32_t fc[EX_MAXW];
+    uint8_t fk[EX_MAXW];
+    int nf = 0;
+    if (active) {
+        uint32_t draw = 0;
+        const uint32_t M = P.nchan, W = (uint32_t)weight;
+        for (uint32_t j = M - W; j < M; ++j) {
+            const uint32_t t = exact_bounded(shot, draw, j + 1, P.k0, P.k1);
+            bool present = false;
+            for (int k = 0; k < nf; ++k) present |= (fc[k] == t);
+            const uint32_t v = present ? j : t;
+            int k = nf;
+            while (k > 0 && fc[k - 1] > v) { fc[k] = fc[k - 1]; --k; }
+            fc[k] = v;
+            ++nf;
+        }
+        for (int k = 0; k < nf; ++k) fk[k] = (uint8_t)exact_code(P.chan_kind[fc[k]], fc[k], shot, P.k0, P.k1);
+    }
+    uint64_t x[2] = {0, 0}, z[2] = {0, 0};
+    bool rej = false;
+    int ptr = 0;
+    for (uint32_t base = 0; base < P.nops; base += PRE_CHUNK) {
+        const uint32_t cnt = min((uint32_t)PRE_CHUNK, P.nops - base);
+        __syncthreads();
+        for (uint32_t k = threadIdx.x; k < cnt; k += EX_THREADS) chunk[k] = P.prog[base + k];
+        __syncthreads();
+        if (!active) continue;
+        for (uint32_t k = 0; k < cnt; ++k) {
+            const PreOp op = chunk[k];
+            const uint32_t kind = op.w0 & 15u;
+            const uint32_t a = (op.w0 >> 4) & 0xFFFu, b = op.w0 >> 16;
+            switch (kind) {
+                case P_H: { const bool xa = bit2(x, a), za = bit2(z, a); flip2(x, a, xa ^ za); flip2(z, a, xa ^ za); break; }
+                case P_S: flip2(z, a, bit2(x, a)); break;
+                case P_CX: flip2(x, b, bit2(x, a)); flip2(z, a, bit2(z, b)); break;
+                case P_CZ: { const bool xa = bit2(x, a), xb = bit2(x, b); flip2(z, a, xb); flip2(z, b, xa); break; }
+                case P_SWAP: {
+                    const bool xa = bit2(x, a), za = bit2(z, a), xb = bit2(x, b), zb = bit2(z, b);
+                    flip2(x, a, xa ^ xb); flip2(x, b, xa ^ xb); flip2(z, a, za ^ zb); flip2(z, b, za ^ zb);
+                    break;
+                }
+                case P_DEP1: case P_DEP2: case P_XERR: {
+                    if (ptr < nf && fc[ptr] == op.w1) {
+                        const uint32_t code = fk[ptr++];
+                        uint32_t px, pz;
+                        if (kind == P_DEP2) {
+                            pauli_xz(code >> 2, px, pz); flip2(x, a, px); flip2(z, a, pz);
+                            pauli_xz(code & 3, px, pz); flip2(x, b, px); flip2(z, b, pz);
+                        } else {
+                            pauli_xz(code, px, pz); flip2(x, a, px); flip2(z, a, pz);
+                        }
+                    }
+                    break;
+                }
+                case P_MDEC: rej |= bit2(x, a); clr2(x, a); clr2(z, a); break;
+                case P_CLEAR: clr2(x, a); clr2(z, a); break;
+                default: break;
+            }
+        }
+    }
+    // kept bits: lane l of a warp holds shot 32*warp_index + l; two warps make a 64-shot word
+    const unsigned ballot = __ballot_sync(0xFFFFFFFFu, active && !rej);
+    const uint64_t word = i >> 6;
+    if ((threadIdx.x & 31) == 0 && (i < P.nshots)) {
+        const int half = (int)((i >> 5) & 1);
+        atomicOr(reinterpret_cast<unsigned long long*>(P.kept) + word, (unsigned long long)ballot << (32 * half));
+    }
+    if (active) {
+        atomicAdd(&hd, 1ull);
+        if (!rej) atomicAdd(&hk, 1ull);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int wb = min(weight, P.wmax);
+        if (hd) atomicAdd(&P.hist_drawn[wb], hd);
+        if (hk) atomicAdd(&P.hist_kept[wb], hk);
+    }
+}
+
 // ---- survivor compaction: count per chunk, scan, write in shot order ----------------------------
 constexpr int CMP_THREADS = 256;
 constexpr int CMP_WORDS = 4;  // words per thread
@@ -379,7 +476,9 @@ qc_status prescreen_run(CircuitImpl& c, qc_noise noise, uint64_t shot0, uint64_t
                         qc_survivors* survivors, uint64_t* hist_drawn, uint64_t* hist_kept, int32_t w_max,
                         cudaStream_t s) {
     if (!(noise.p >= 0.0 && noise.p < 1.0)) return fail(QC_EINVAL, "p must lie in [0, 1)");
-    if (noise.fault_weight >= 0) return fail(QC_EINVAL, "the pre-screen takes Bernoulli noise (fault_weight = -1)");
+    if (noise.fault_weight >= 0 && (noise.fault_weight > EX_MAXW || (uint64_t)noise.fault_weight > c.chan_kind.size()))
+        return fail(QC_EINVAL, "fixed fault weight must lie in [0, min(%d, channels)]", EX_MAXW);
+    if (noise.fault_weight >= 0 && c.n > 128) return fail(QC_EINVAL, "fixed-weight pre-screen supports up to 128 qubits");
     if (shot0 % 64) return fail(QC_EINVAL, "shot0 must be a multiple of 64");
     if ((shot0 + nshots) / 64 >= (1ull << 32)) return fail(QC_EINVAL, "shot index beyond the 2^38 range of the contract");
     if (w_max < 0 || w_max >= WMAX_BINS) return fail(QC_EINVAL, "w_max must lie in [0, 63]");
@@ -428,8 +527,15 @@ qc_status prescreen_run(CircuitImpl& c, qc_noise noise, uint64_t shot0, uint64_t
         if (smem > 227 * 1024) { out = fail(QC_EINVAL, "too many qubits for the pre-screen frame (%d)", c.n); break; }
         e = cudaFuncSetAttribute(prescreen_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) { out = cuda_fail(e, "cudaFuncSetAttribute"); break; }
-        const uint64_t blocks = (nwords + PRE_THREADS - 1) / PRE_THREADS;
-        prescreen_kernel<<<(unsigned)blocks, PRE_THREADS, smem, s>>>(P);
+        if (noise.fault_weight >= 0) {
+            e = cudaMemsetAsync(kept_mask_dev, 0, nwords * sizeof(uint64_t), s);
+            if (e != cudaSuccess) { out = cuda_fail(e, "memset"); break; }
+            prescreen_exact_kernel<<<(unsigned)((nshots + EX_THREADS - 1) / EX_THREADS), EX_THREADS, 0, s>>>(
+                P, noise.fault_weight);
+        } else {
+            const uint64_t blocks = (nwords + PRE_THREADS - 1) / PRE_THREADS;
+            prescreen_kernel<<<(unsigned)blocks, PRE_THREADS, smem, s>>>(P);
+        }
         e = cudaGetLastError();
         if (e != cudaSuccess) { out = cuda_fail(e, "prescreen_kernel"); break; }
         uint64_t total = 0;

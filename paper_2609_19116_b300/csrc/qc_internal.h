@@ -70,6 +70,11 @@ struct RefKey {
         return cutoff < o.cutoff;
     }
 };
+struct RefPacked {  // the slot layout of a smaller capacity bucket
+    void* state = nullptr;  // unused
+    int* cap = nullptr;
+    uint64_t* off = nullptr;
+};
 struct RefState {
     void* state = nullptr;     // one slot of site tensors
     int* dims = nullptr;       // [n+1] bond dimensions, device
@@ -77,6 +82,7 @@ struct RefState {
     uint64_t* off = nullptr;   // [n+1] site offsets, device
     double disc = 0, norm = 0;
     int chi_peak = 0;
+    std::map<int, RefPacked> packed;  // by slot capacity
 };
 
 struct CircuitImpl {
@@ -119,7 +125,7 @@ qc_status prescreen_run(CircuitImpl& c, qc_noise noise, uint64_t shot0, uint64_t
                         cudaStream_t s);
 qc_status engine_launch(CircuitImpl& c, qc_noise noise, const uint64_t* shots_dev, uint64_t nshots,
                         qc_mps_params prm, unsigned long long* counts_dev, int wmax, qc_shot_result* per_shot,
-                        cudaStream_t s, int max_slots);
+                        cudaStream_t s, int max_slots, bool shared_gpu);
 qc_status shot_footprint(const CircuitImpl& c, qc_mps_params prm, uint64_t* bytes);
 
 // Pauli code conventions.

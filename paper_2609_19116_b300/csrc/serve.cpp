@@ -155,7 +155,7 @@ struct Server {
             const int slots = (int)std::max<uint64_t>(1, bytes / std::max<uint64_t>(1, j->footprint));
             if (st == QC_OK)
                 st = engine_launch(*j->circ, j->noise, j->surv_dev + first, count, j->prm, counts, WBINS - 1, nullptr, s,
-                                   slots);
+                                   slots, true);
             if (st == QC_OK && (cudaMemcpyAsync(h, counts, sizeof h, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
                                 cudaStreamSynchronize(s) != cudaSuccess))
                 st = fail(QC_EDEVICE, "engine chunk");

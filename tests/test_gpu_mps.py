@@ -163,3 +163,19 @@ def test_d5_workload_c64_sampled_shots(chi_max):
     sub = res[np.isin(res["shot"], pick)]
     _compare(sub, ref, 1e-4, allow_flip=1)
     assert (res["status"] >= 0).all()
+
+
+def test_capacity_bucket_rerun(monkeypatch):
+    """Slots sized below the shots' bond dimensions: the first pass reports the shots that outgrow
+    them, the second pass re-runs those with the full capacity; results equal a single pass."""
+    q = lib_ready()
+    text = workload_circuit("d3_17q_12l", layers=6)
+    c = q.Circuit(text)
+    shots = list(range(64, 64 + 150))
+    c1, r1 = q.mps_sample_batch(c, dev_shots(shots), p=4e-3, seed=2, chi_max=32, cutoff=1e-12, precision=q.QC_C128)
+    monkeypatch.setenv("QCMPS_CHI_ALLOC", "4")
+    c2, r2 = q.mps_sample_batch(c, dev_shots(shots), p=4e-3, seed=2, chi_max=32, cutoff=1e-12, precision=q.QC_C128)
+    assert np.array_equal(c1, c2)
+    assert np.array_equal(r1["status"], r2["status"]) and np.array_equal(r1["shot"], r2["shot"])
+    assert np.allclose(r1["fidelity"], r2["fidelity"], atol=1e-10)
+    assert (r2["chi_peak"] > 4).any()

@@ -123,3 +123,23 @@ def test_prescreen_full_size_sampled(p):
         assert bool((int(mask[s >> 6]) >> (s & 63)) & 1) == kept[s], s
     assert out["hist_drawn"].sum() == n
     assert out["hist_kept"].sum() == sum(int(w).bit_count() for w in mask)
+
+
+@pytest.mark.parametrize("w", [1, 3, 5])
+def test_prescreen_fixed_weight_bit_exact(w):
+    """Subset sampling (Sec. 4.1): every shot has exactly w faults; kept flags equal the oracle's."""
+    q = lib_ready()
+    text = workload_circuit("d5_49q_60l", layers=10)
+    c = q.Circuit(text)
+    n = 64 * 40 + 17
+    out = q.pauli_prescreen(c, 64 * 3, n, p=0.0, seed=21, fault_weight=w)
+    got = kept_bits(out["kept_mask"], n)
+    oc = parse(text)
+    shots = range(64 * 3, 64 * 3 + n)
+    faults = sampler.draw_faults(oc, p=0.0, seed=21, shots=shots, fault_weight=w)
+    kept = prescreen.frame_prescreen(oc, prescreen.decided_measurements(oc), faults)
+    exp = np.array([kept[s] for s in shots], dtype=bool)
+    assert np.array_equal(got, exp)
+    assert out["n_kept"] == exp.sum()
+    assert np.array_equal(out["survivors"].cpu().numpy(), np.array([s for s in shots if kept[s]], dtype=np.int64))
+    assert out["hist_drawn"][w] == n and out["hist_kept"][w] == exp.sum()
