@@ -430,7 +430,7 @@ def main():
         "gpu_launches": args.steps * 5,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                      "frac": achieved / alu_peak if alu_peak else None, "traffic": None,
-                     "kernel": "engine_kernel<float,512>",
+                     "kernel": "engine_kernel<float,32> (one warp per shot)",
                      "peak_note": "FP32 FMA issue rate 148 SM x 128 lanes x 2 x sm_max_mhz (MEASURED_PEAKS sm_max_mhz)",
                      "alg_flops_per_shot": flops_last / max(1, last["n"]), "engine_ms": eng_ms},
         "clocks": clocks,

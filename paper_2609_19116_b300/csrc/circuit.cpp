@@ -303,11 +303,11 @@ static void compile_mps(CircuitImpl& c) {
     int center = 0;
     auto move_to = [&](int t) {
         while (center < t) {
-            c.mps.push_back({M_G2, F_CENTER_RIGHT, (uint16_t)center, G4_ID, 0, -1});
+            c.mps.push_back({M_MOVE, F_CENTER_RIGHT, (uint16_t)center, 0, 0, -1});
             ++center;
         }
         while (center > t) {
-            c.mps.push_back({M_G2, 0, (uint16_t)(center - 1), G4_ID, 0, -1});
+            c.mps.push_back({M_MOVE, 0, (uint16_t)(center - 1), 0, 0, -1});
             --center;
         }
     };
@@ -328,7 +328,7 @@ static void compile_mps(CircuitImpl& c) {
         }
     }
     c.n_updates = 0;
-    for (const MpsOp& m : c.mps) c.n_updates += (m.kind == M_G2);
+    for (const MpsOp& m : c.mps) c.n_updates += (m.kind == M_G2 || m.kind == M_MOVE);
 }
 
 CircuitImpl::~CircuitImpl() {

@@ -236,7 +236,7 @@ struct Engine {
     // Pairs whose smaller column is below the numerical floor are left alone: such a column is
     // rounding noise of a rank-deficient theta, and rotating it against a large column never
     // reaches relative orthogonality.
-    __device__ bool jacobi(V* X, int rows, int cols, int ld, R floor2) {
+    __device__ bool jacobi(V* X, int rows, int cols, int ld, R floor2, V* Vm = nullptr, int vdim = 0) {
         const int lane = tid_ & 31, wid = tid_ >> 5;
         constexpr int NW = NT / 32;
         const R eps = sizeof(R) == 4 ? (R)FLT_EPSILON : (R)DBL_EPSILON;
@@ -288,6 +288,17 @@ struct Engine {
                             a[i] = cmk<V>(c * x.x - sn * emx, c * x.y - sn * emy);
                             b[i] = cmk<V>(sn * epx + c * y.x, sn * epy + c * y.y);
                         }
+                        if (Vm) {  // the same rotation on the accumulated right factor (vdim x vdim)
+                            V* va = Vm + (size_t)ca * vdim;
+                            V* vb = Vm + (size_t)cb * vdim;
+                            for (int i = gl; i < vdim; i += g) {
+                                const V x = va[i], y = vb[i];
+                                const R emx = er * y.x + ei * y.y, emy = er * y.y - ei * y.x;
+                                const R epx = er * x.x - ei * x.y, epy = er * x.y + ei * x.x;
+                                va[i] = cmk<V>(c * x.x - sn * emx, c * x.y - sn * emy);
+                                vb[i] = cmk<V>(sn * epx + c * y.x, sn * epy + c * y.y);
+                            }
+                        }
                     }
                 }
                 bsync<NT>();
@@ -296,6 +307,78 @@ struct Engine {
             if (!bsync_or<NT>(rotated)) return true;
         }
         return false;
+    }
+
+    // ---- singular values of the orthogonalised columns: norms, descending order (ties: lower
+    //      index first), truncation rule in FP64.  Returns the kept count r; S.red[41] holds the
+    //      renormalisation factor.
+    __device__ int spectrum(V* X, int rows, int cols, int ld, R* sig2, int* perm, R floor2) {
+        // singular values: column norms, then descending order (ties: lower index first)
+        {
+            const int lane = tid_ & 31, wid = tid_ >> 5;
+            constexpr int NW = NT / 32;
+            const int cpw = (cols + NW - 1) / NW;
+            int G = 1;
+            while (G < cpw && G < 32) G <<= 1;
+            const int g = 32 / G, grp = lane / g, gl = lane - grp * g;
+            for (int base = wid * G; base < cols; base += NW * G) {
+                const int j = base + grp;
+                R sq = 0;
+                if (j < cols) {
+                    const V* col = X + (size_t)j * ld;
+                    for (int i = gl; i < rows; i += g) sq = fma(col[i].x, col[i].x, fma(col[i].y, col[i].y, sq));
+                }
+                for (int o = g >> 1; o > 0; o >>= 1) sq += __shfl_xor_sync(0xFFFFFFFFu, sq, o);
+                if (j < cols && gl == 0) sig2[j] = sq;
+            }
+        }
+        bsync<NT>();
+        for (int j = tid_; j < cols; j += NT) {
+            const R sj = sig2[j];
+            int rk = 0;
+            for (int k = 0; k < cols; ++k) {
+                const R sk = sig2[k];
+                rk += (sk > sj) || (sk == sj && k < j);
+            }
+            perm[rk] = j;
+        }
+        bsync<NT>();
+        // truncation rule, FP64: smallest r >= 1 with discarded tail <= cutoff * total, r <= chi_max
+        if (tid_ == 0) {
+            double tot = 0;
+            int nz = 0;
+            for (int k = 0; k < cols; ++k) {
+                tot += (double)sig2[k];
+                nz += sig2[k] > floor2;
+            }
+            const double thr = P.cutoff * tot;
+            int r = cols;
+            double tail = 0;
+            while (r > 1 && tail + (double)sig2[perm[r - 1]] <= thr) {
+                tail += (double)sig2[perm[r - 1]];
+                --r;
+            }
+            while (r > P.chi_trunc || (r > 1 && r > nz)) {
+                tail += (double)sig2[perm[r - 1]];
+                --r;
+            }
+            double kept = 0;
+            for (int k = 0; k < r; ++k) kept += (double)sig2[perm[k]];
+            int dg = 0;
+            if (r < cols) {
+                const double sa = sqrt((double)sig2[perm[r - 1]]), sb = sqrt((double)sig2[perm[r]]);
+                dg = (sb > 0 && sa / sb - 1.0 < 1e-8);
+            }
+            S.red[40] = tot > 0 ? tail / tot : 0.0;
+            S.red[41] = kept > 0 ? 1.0 / sqrt(kept) : 0.0;
+            S.red[42] = (double)r;
+            S.red[43] = (double)dg;
+        }
+        bsync<NT>();
+        const int r = (int)S.red[42];
+        disc += S.red[40];
+        degen += (int)S.red[43];
+        return r;
     }
 
     __device__ void release_big(bool locked) {
@@ -414,71 +497,7 @@ struct Engine {
             release_big(locked);
             return;
         }
-        // singular values: column norms, then descending order (ties: lower index first)
-        {
-            const int lane = tid_ & 31, wid = tid_ >> 5;
-            constexpr int NW = NT / 32;
-            const int cpw = (cols + NW - 1) / NW;
-            int G = 1;
-            while (G < cpw && G < 32) G <<= 1;
-            const int g = 32 / G, grp = lane / g, gl = lane - grp * g;
-            for (int base = wid * G; base < cols; base += NW * G) {
-                const int j = base + grp;
-                R sq = 0;
-                if (j < cols) {
-                    const V* col = X + (size_t)j * ld;
-                    for (int i = gl; i < rows; i += g) sq = fma(col[i].x, col[i].x, fma(col[i].y, col[i].y, sq));
-                }
-                for (int o = g >> 1; o > 0; o >>= 1) sq += __shfl_xor_sync(0xFFFFFFFFu, sq, o);
-                if (j < cols && gl == 0) sig2[j] = sq;
-            }
-        }
-        bsync<NT>();
-        for (int j = tid_; j < cols; j += NT) {
-            const R sj = sig2[j];
-            int rk = 0;
-            for (int k = 0; k < cols; ++k) {
-                const R sk = sig2[k];
-                rk += (sk > sj) || (sk == sj && k < j);
-            }
-            perm[rk] = j;
-        }
-        bsync<NT>();
-        // truncation rule, FP64: smallest r >= 1 with discarded tail <= cutoff * total, r <= chi_max
-        if (tid_ == 0) {
-            double tot = 0;
-            int nz = 0;
-            for (int k = 0; k < cols; ++k) {
-                tot += (double)sig2[k];
-                nz += sig2[k] > floor2;
-            }
-            const double thr = P.cutoff * tot;
-            int r = cols;
-            double tail = 0;
-            while (r > 1 && tail + (double)sig2[perm[r - 1]] <= thr) {
-                tail += (double)sig2[perm[r - 1]];
-                --r;
-            }
-            while (r > P.chi_trunc || (r > 1 && r > nz)) {
-                tail += (double)sig2[perm[r - 1]];
-                --r;
-            }
-            double kept = 0;
-            for (int k = 0; k < r; ++k) kept += (double)sig2[perm[k]];
-            int dg = 0;
-            if (r < cols) {
-                const double sa = sqrt((double)sig2[perm[r - 1]]), sb = sqrt((double)sig2[perm[r]]);
-                dg = (sb > 0 && sa / sb - 1.0 < 1e-8);
-            }
-            S.red[40] = tot > 0 ? tail / tot : 0.0;
-            S.red[41] = kept > 0 ? 1.0 / sqrt(kept) : 0.0;
-            S.red[42] = (double)r;
-            S.red[43] = (double)dg;
-        }
-        bsync<NT>();
-        const int r = (int)S.red[42];
-        disc += S.red[40];
-        degen += (int)S.red[43];
+        const int r = spectrum(X, rows, cols, ld, sig2, perm, floor2);
         const R scale = (R)S.red[41];
         if (r > P.cap[q + 1]) {
             status = QC_ECAPACITY;
@@ -535,6 +554,126 @@ struct Engine {
             const double M = (double)max(m, n), Nn = (double)min(m, n);
             flops += 8.0 * m * cm * n + 128.0 * cl * cr + 4.0 * (4.0 * M * M * Nn + 22.0 * Nn * Nn * Nn) +
                      8.0 * r * m * n;
+        }
+    }
+
+    // ---- centre move between q and q+1 without a gate: split one site tensor ----------------------
+    // Right: one-sided Jacobi on the columns of A[q] (m x cm) with the rotations accumulated in V
+    // (cm x cm); A[q] V = U S gives A[q] = U and the centre S V^H A[q+1].  Left: the same on A[q+1]^H,
+    // A[q+1] = V S U'^H gives A[q+1] = U'^H and the centre A[q] V S.  The singular values equal
+    // those of the two-site theta (the neighbour is canonical), so the truncation rule applies as in
+    // a two-site update.
+    __device__ void move(int q, bool right) {
+        bsync<NT>();
+        const int cl = S.dims[q], cm = S.dims[q + 1], cr = S.dims[q + 2];
+        const int m = 2 * cl, n = 2 * cr;
+        // the round-robin ordering needs an even column count: an odd bond gets a zero column,
+        // which is never rotated and is dropped as numerically zero
+        const int rows = right ? m : n, cols = cm + (cm & 1);
+        const int ld = rows + 1;
+        const uint64_t other = right ? (uint64_t)cm * n : (uint64_t)m * cm;
+        const uint64_t sgw = ((uint64_t)cols * (sizeof(R) + sizeof(int)) + sizeof(V) - 1) / sizeof(V);
+        const bool fast = (uint64_t)ld * cols + (uint64_t)cm * cm + other + sgw <= P.x_smem;
+        V* X = fast ? S.X : xg;
+        V* Vm = X + (size_t)ld * cols;
+        V* O = fast ? Vm + (size_t)cm * cm : nullptr;  // staged copy of the other tensor
+        R* sig2 = fast ? reinterpret_cast<R*>(O + other) : gsig2;
+        int* perm = reinterpret_cast<int*>(sig2 + cols);
+        V* A = site(q);
+        V* B = site(q + 1);
+        double fro = 0;
+        if (right) {
+            for (int e = tid_; e < m * cm; e += NT) {
+                const int i = e / cm, j = e - i * cm;
+                const V v = A[e];
+                X[(size_t)j * ld + i] = v;
+                fro += (double)v.x * v.x + (double)v.y * v.y;
+            }
+            if (fast) for (int e = tid_; e < cm * n; e += NT) O[e] = B[e];
+        } else {
+            for (int e = tid_; e < cm * n; e += NT) {
+                const int k = e / n, j = e - k * n;
+                const V v = B[e];
+                X[(size_t)k * ld + j] = cmk<V>(v.x, -v.y);
+                fro += (double)v.x * v.x + (double)v.y * v.y;
+            }
+            if (fast) for (int e = tid_; e < m * cm; e += NT) O[e] = A[e];
+        }
+        for (int e = tid_; e < cm * cm; e += NT) {
+            const int a = e / cm, b = e - a * cm;
+            Vm[e] = cmk<V>(a == b ? (R)1 : (R)0, (R)0);
+        }
+        if (cols > cm)
+            for (int i = tid_; i < rows; i += NT) X[(size_t)cm * ld + i] = cmk<V>(0, 0);
+        const V* Bo = right ? (fast ? O : B) : B;
+        const V* Ao = right ? A : (fast ? O : A);
+        fro = block_sum<NT>(fro, S.red, tid_);
+        const R eps = sizeof(R) == 4 ? (R)FLT_EPSILON : (R)DBL_EPSILON;
+        const R fl = (R)4 * eps * sqrt((R)rows);
+        const R floor2 = fl * fl * (R)fro;
+        if (!jacobi(X, rows, cols, ld, floor2, Vm, cm)) {
+            status = QC_ENOCONV;
+            return;
+        }
+        const int r = spectrum(X, rows, cols, ld, sig2, perm, floor2);
+        const R scale = (R)S.red[41];
+        if (r > P.cap[q + 1]) {
+            status = QC_ECAPACITY;
+            return;
+        }
+        for (int e = tid_; e < r * rows; e += NT) {  // the orthonormal factor
+            const int k = e / rows, i = e - k * rows;
+            const R sg = sig2[perm[k]];
+            const R inv = sg > (R)0 ? (R)1 / sqrt(sg) : (R)0;
+            V* col = X + (size_t)perm[k] * ld;
+            col[i] = cmk<V>(col[i].x * inv, col[i].y * inv);
+        }
+        bsync<NT>();
+        if (right) {
+            // A[q] = U (cl, 2, r);  A[q+1] = scale S V^H B (r, 2, cr)
+            for (int e = tid_; e < r * n; e += NT) {
+                const int kk = e / n, j = e - kk * n;
+                const int pc = perm[kk];
+                const V* v = Vm + (size_t)pc * cm;
+                V acc = cmk<V>(0, 0);
+                if (pc < cm)  // the padding column is zero
+                    for (int k = 0; k < cm; ++k) acc = cfmac(v[k], Bo[(size_t)k * n + j], acc);
+                const R f = scale * sqrt(sig2[pc]);
+                tcopy[e] = cmk<V>(acc.x * f, acc.y * f);
+            }
+            bsync<NT>();
+            for (int e = tid_; e < m * r; e += NT) {
+                const int i = e / r, k = e - i * r;
+                A[e] = X[(size_t)perm[k] * ld + i];
+            }
+            for (int e = tid_; e < r * n; e += NT) B[e] = tcopy[e];
+        } else {
+            // A[q+1] = U'^H (r, 2, cr);  A[q] = scale A V S (cl, 2, r)
+            for (int e = tid_; e < m * r; e += NT) {
+                const int i = e / r, kk = e - i * r;
+                const int pc = perm[kk];
+                const V* v = Vm + (size_t)pc * cm;
+                V acc = cmk<V>(0, 0);
+                if (pc < cm)
+                    for (int k = 0; k < cm; ++k) acc = cfma(Ao[(size_t)i * cm + k], v[k], acc);
+                const R f = scale * sqrt(sig2[pc]);
+                tcopy[e] = cmk<V>(acc.x * f, acc.y * f);
+            }
+            bsync<NT>();
+            for (int e = tid_; e < r * n; e += NT) {
+                const int k = e / n, j = e - k * n;
+                const V u = X[(size_t)perm[k] * ld + j];
+                B[e] = cmk<V>(u.x, -u.y);
+            }
+            for (int e = tid_; e < m * r; e += NT) A[e] = tcopy[e];
+        }
+        bsync<NT>();
+        if (tid_ == 0) S.dims[q + 1] = r;
+        bsync<NT>();
+        ++nupd;
+        {
+            const double M = (double)max(rows, cols), Nn = (double)min(rows, cols);
+            flops += 4.0 * (4.0 * M * M * Nn + 22.0 * Nn * Nn * Nn) + 8.0 * r * cm * (right ? n : m);
         }
     }
 
@@ -759,6 +898,9 @@ struct Engine {
                     case M_G2:
                         update(op.q, P.g4 + op.a * 16, (op.flags & F_CENTER_RIGHT) != 0);
                         if (status != 0) abort_op = op.src;
+                        break;
+                    case M_MOVE:
+                        move(op.q, (op.flags & F_CENTER_RIGHT) != 0);
                         break;
                     case M_MEAS:
                     case M_RESET:

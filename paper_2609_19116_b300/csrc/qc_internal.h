@@ -35,7 +35,7 @@ inline PreOp make_preop(uint32_t kind, uint32_t q0, uint32_t q1, uint32_t chan) 
 }
 
 // ---- MPS program ---------------------------------------------------------------------------
-enum MpsKind : uint8_t { M_G1 = 0, M_G2, M_CH1, M_CH2, M_MEAS, M_RESET };
+enum MpsKind : uint8_t { M_G1 = 0, M_G2, M_CH1, M_CH2, M_MEAS, M_RESET, M_MOVE };
 enum MpsFlag : uint8_t { F_CENTER_RIGHT = 1, F_POSTSELECT = 2, F_XERR = 4 };
 struct MpsOp {
     uint8_t kind;
