@@ -47,6 +47,8 @@ def parse_args():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-comparator", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=5.0)
+    ap.add_argument("--case", default=None, choices=["engine-prefix6", "prescreen-1e7"],
+                    help="run one small profiling case once and print its timing (for ncu captures)")
     return ap.parse_args()
 
 
@@ -273,8 +275,43 @@ def comparator_leg(q, text, circ, shot, args, time_cap_s=40.0):
 
 
 # ---- the GPU arm ------------------------------------------------------------------------------
+def profiling_case(args):
+    """Small, self-contained cases for ncu: the MPS engine on the 6-layer prefix of the 49-qubit
+    workload with 1,332 survivors (every shot slot of one launch busy), or the pre-screen on 1e7
+    shots of the 200-layer circuit."""
+    import numpy as np
+    import torch
+    import paper_2609_19116_b300 as q
+    from synth import workload_circuit
+    if args.case == "engine-prefix6":
+        c = q.Circuit(workload_circuit(WORKLOAD, seed=args.seed, layers=6))
+        surv = q.pauli_prescreen(c, 0, 64 * 20000, p=args.p, seed=args.seed)["survivors"][:1332]
+        q.mps_sample_batch(c, surv[:1], p=args.p, seed=args.seed, chi_max=args.chi_max, cutoff=args.cutoff)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        counts, res = q.mps_sample_batch(c, surv, p=args.p, seed=args.seed, chi_max=args.chi_max, cutoff=args.cutoff)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t
+        print(json.dumps({"case": args.case, "shots": int(surv.numel()), "seconds": dt,
+                          "updates": int(res["n_updates"].sum()), "alg_flops": float(res["alg_flops"].sum()),
+                          "sweeps_per_update": float(res["sweeps"].sum() / max(1, res["n_updates"].sum()))}))
+    else:
+        c = q.Circuit(workload_circuit("d5_49q_200l", seed=args.seed))
+        q.pauli_prescreen(c, 0, 64 * 1024, p=args.p, seed=args.seed, survivors_capacity=0)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        out = q.pauli_prescreen(c, 0, 10**7, p=args.p, seed=args.seed, survivors_capacity=0)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t
+        print(json.dumps({"case": args.case, "shots": 10**7, "seconds": dt, "kept": int(out["n_kept"]),
+                          "frame_instructions": c.info()["n_ops"]}))
+
+
 def main():
     args = parse_args()
+    if args.case:
+        profiling_case(args)
+        return
     if args.impl == "reference":
         run_reference(args)
         return
