@@ -47,6 +47,8 @@ def parse_args():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-comparator", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=5.0)
+    ap.add_argument("--subsets", action="store_true",
+                    help="also run the subset-sampling leg: exactly k faults, k = 0..4, chi_max 1024")
     ap.add_argument("--case", default=None, choices=["engine-prefix6", "prescreen-1e7"],
                     help="run one small profiling case once and print its timing (for ncu captures)")
     return ap.parse_args()
@@ -274,6 +276,37 @@ def comparator_leg(q, text, circ, shot, args, time_cap_s=40.0):
             "extrapolated": extrapolated, "status": st}
 
 
+# ---- subset sampling at large bond (exactly k faults per shot, Sec. 4.1) ---------------------------
+def subsets_leg(q, np, circ, args, target=1024, chi=1024):
+    """For k = 0..4: fixed-weight pre-screen of drawn shots until `target` survivors, then the engine
+    on them at chi_max 1024 (complex64); per k the counts and accepted shots/s of the engine."""
+    import torch
+    out = {}
+    for k in range(5):
+        surv, drawn, base = [], 0, 64 * (1 << 24) * (k + 1)
+        while len(surv) < target and drawn < 64 * 200000:
+            n = 64 * 16384
+            pre = q.pauli_prescreen(circ, base + drawn, n, p=0.0, seed=args.seed, fault_weight=k)
+            surv += pre["survivors"].cpu().tolist()
+            drawn += n
+        surv = surv[:target]
+        dev = torch.tensor(surv, dtype=torch.int64, device="cuda")
+        q.mps_sample_batch(circ, dev[:1], p=0.0, seed=args.seed, chi_max=chi, cutoff=args.cutoff, fault_weight=k,
+                           per_shot=False)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        counts, res = q.mps_sample_batch(circ, dev, p=0.0, seed=args.seed, chi_max=chi, cutoff=args.cutoff,
+                                         fault_weight=k)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        acc = int(counts[:, 1].sum())
+        out[str(k)] = {"drawn": drawn, "survivors": len(surv), "accepted": acc,
+                       "logical_errors": int(counts[:, 2].sum()), "seconds": dt,
+                       "accepted_shots_per_s": acc / dt if dt > 0 else None,
+                       "chi_peak": int(res["chi_peak"].max()), "max_discarded": float(res["discarded"].max())}
+    return {"chi_max": chi, "target_survivors_per_k": target, "per_k": out}
+
+
 # ---- the GPU arm ------------------------------------------------------------------------------
 def profiling_case(args):
     """Small, self-contained cases for ncu: the MPS engine on the 6-layer prefix of the 49-qubit
@@ -441,6 +474,7 @@ def main():
     if not args.no_serving and world == 1:
         circ17 = q.Circuit(workload_circuit("d3_17q_12l", seed=args.seed))
         serving = serving_leg(q, np, circ17, circ, duration_s=args.serve_seconds)
+    subsets = subsets_leg(q, np, circ, args) if args.subsets else None
     comparator = None
     if not args.no_comparator:
         comparator = comparator_leg(q, text, circ, int(res["shot"][0]), args)
@@ -476,6 +510,7 @@ def main():
         "cpu_baseline": cpu,
         "serving": serving,
         "plain_fp64_gpu": comparator,
+        "subsets": subsets,
         "wall_s": wall,
     }
     print(json.dumps(line), flush=True)

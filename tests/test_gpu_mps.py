@@ -179,3 +179,21 @@ def test_capacity_bucket_rerun(monkeypatch):
     assert np.array_equal(r1["status"], r2["status"]) and np.array_equal(r1["shot"], r2["shot"])
     assert np.allclose(r1["fidelity"], r2["fidelity"], atol=1e-10)
     assert (r2["chi_peak"] > 4).any()
+
+
+def test_subset_sampling_chi1024_matches_oracle():
+    """Config 5 shape: the 49-qubit workload with exactly k faults per shot at chi_max 1024 (slot
+    capacity bucketed from the reference's chi_peak), survivors of the fixed-weight pre-screen,
+    recomputed by the FP64 oracle MPS."""
+    q = lib_ready()
+    text = workload_circuit("d5_49q_60l", layers=12)
+    c = q.Circuit(text)
+    for k in (0, 2):
+        pre = q.pauli_prescreen(c, 0, 64 * 8, p=0.0, seed=7, fault_weight=k)
+        shots = pre["survivors"].cpu().numpy()[:3]
+        assert len(shots) >= 1
+        _, res = q.mps_sample_batch(c, dev_shots(shots), p=0.0, seed=7, chi_max=1024, cutoff=1e-10,
+                                    precision=q.QC_C64, fault_weight=k)
+        assert (res["weight"] == k).all()
+        ref = _oracle_results(text, [int(s) for s in shots], p=0.0, seed=7, engine="mps", weight=k, cutoff=1e-10)
+        _compare(res, ref, 1e-4, allow_flip=1)
