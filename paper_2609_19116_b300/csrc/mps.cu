@@ -236,7 +236,8 @@ struct Engine {
     // Pairs whose smaller column is below the numerical floor are left alone: such a column is
     // rounding noise of a rank-deficient theta, and rotating it against a large column never
     // reaches relative orthogonality.
-    __device__ bool jacobi(V* X, int rows, int cols, int ld, R floor2, V* Vm = nullptr, int vdim = 0) {
+    __device__ bool jacobi(V* X, int rows, int cols, int ld, R floor2, V* Vm = nullptr, int vdim = 0,
+                           int max_sweeps = 0, int* any_rotation = nullptr) {
         const int lane = tid_ & 31, wid = tid_ >> 5;
         constexpr int NW = NT / 32;
         const R eps = sizeof(R) == 4 ? (R)FLT_EPSILON : (R)DBL_EPSILON;
@@ -247,7 +248,8 @@ struct Engine {
         while (G < ppw && G < 32) G <<= 1;
         while (G > 1 && 32 / G < 2 && rows > 32 / G) G >>= 1;  // keep at least 2 lanes per pair when useful
         const int g = 32 / G, grp = lane / g, gl = lane - grp * g;
-        for (int sweep = 0; sweep < P.sweep_cap; ++sweep) {
+        const int cap = max_sweeps > 0 ? max_sweeps : P.sweep_cap;
+        for (int sweep = 0; sweep < cap; ++sweep) {
             int rotated = 0;
             for (int k = 0; k < cm1; ++k) {
                 for (int base = wid * G; base < half; base += NW * G) {
@@ -303,8 +305,55 @@ struct Engine {
                 }
                 bsync<NT>();
             }
+            if (max_sweeps == 0) ++sweeps;
+            const int any = bsync_or<NT>(rotated);
+            if (any && any_rotation) *any_rotation = 1;
+            if (!any) return true;
+        }
+        return max_sweeps > 0;  // an inner pass is not required to converge on its own
+    }
+
+    // ---- block Jacobi for an X that lives in global memory ----------------------------------------
+    // The columns are cut into blocks of bw that fit twice into the shared work area; blocks are
+    // paired round-robin, each pair is copied into shared memory once per outer round, all column
+    // pairs inside it are rotated there (a few inner sweeps), and the pair is written back.  Global
+    // traffic per outer sweep drops by about bw against rotating column pairs in place.
+    __device__ bool jacobi_blocked(V* X, int rows, int cols, int ld, R floor2, V* W, int bw) {
+        const int lw = rows + 1;
+        const int nb = (cols + bw - 1) / bw;
+        const int nbp = nb + (nb & 1);  // an even number of blocks (the last may be a dummy)
+        for (int sweep = 0; sweep < P.sweep_cap; ++sweep) {
+            int rot = 0;
+            for (int k = 0; k < nbp - 1; ++k) {
+                for (int pr = 0; pr < nbp / 2; ++pr) {
+                    const int sa = pr, sb = nbp - 1 - pr;
+                    const int bi = sa == 0 ? 0 : 1 + (sa - 1 + k) % (nbp - 1);
+                    const int bj = 1 + (sb - 1 + k) % (nbp - 1);
+                    const int i0 = bi * bw, i1 = min(cols, i0 + bw);
+                    const int j0 = bj * bw, j1 = min(cols, j0 + bw);
+                    const int ni = bi < nb ? i1 - i0 : 0, nj = bj < nb ? j1 - j0 : 0;
+                    if (ni + nj < 2) continue;
+                    const int nc = ni + nj, ncp = nc + (nc & 1);
+                    for (int e = tid_; e < ncp * rows; e += NT) {
+                        const int c = e / rows, i = e - c * rows;
+                        V v = cmk<V>(0, 0);
+                        if (c < ni) v = X[(size_t)(i0 + c) * ld + i];
+                        else if (c < nc) v = X[(size_t)(j0 + c - ni) * ld + i];
+                        W[(size_t)c * lw + i] = v;
+                    }
+                    bsync<NT>();
+                    jacobi(W, rows, ncp, lw, floor2, nullptr, 0, 3, &rot);
+                    for (int e = tid_; e < nc * rows; e += NT) {
+                        const int c = e / rows, i = e - c * rows;
+                        const V v = W[(size_t)c * lw + i];
+                        if (c < ni) X[(size_t)(i0 + c) * ld + i] = v;
+                        else X[(size_t)(j0 + c - ni) * ld + i] = v;
+                    }
+                    bsync<NT>();
+                }
+            }
             ++sweeps;
-            if (!bsync_or<NT>(rotated)) return true;
+            if (!rot) return true;
         }
         return false;
     }
@@ -492,7 +541,9 @@ struct Engine {
         const R eps = sizeof(R) == 4 ? (R)FLT_EPSILON : (R)DBL_EPSILON;
         const R fl = (R)4 * eps * sqrt((R)rows);
         const R floor2 = fl * fl * (R)fro;
-        if (!jacobi(X, rows, cols, ld, floor2)) {
+        const int bw = (int)(P.x_smem / (2 * (uint32_t)(rows + 1)));
+        const bool blocked = (X == xg) && bw >= 2 && bw * 2 < cols;
+        if (!(blocked ? jacobi_blocked(X, rows, cols, ld, floor2, S.X, bw) : jacobi(X, rows, cols, ld, floor2))) {
             status = QC_ENOCONV;
             release_big(locked);
             return;
@@ -993,7 +1044,7 @@ __device__ unsigned char* carve(Shared<R>& S, unsigned char* p, const EnginePara
 // Persistent engine.  CTA mode (NT > 32): the CTA is one engine.  Warp mode (NT = 32): every warp
 // of the CTA is an engine with its own shot slot, and the warps share one large work area.
 template <typename R, int NT>
-__global__ void __launch_bounds__(NT == 32 ? 256 : NT, NT == 32 ? 1 : (NT == 128 ? 4 : (NT == 256 ? 2 : 1)))
+__global__ void __launch_bounds__(NT == 32 ? 256 : NT, NT == 32 ? 2 : (NT == 128 ? 4 : (NT == 256 ? 2 : 1)))
 engine_kernel(const EngineParams<R> P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int engines = (NT == 32) ? (int)(blockDim.x >> 5) : 1;
