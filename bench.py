@@ -235,7 +235,8 @@ def serving_leg(q, np, circ17, circ49, duration_s=5.0, rate=50.0, seed=0, drain_
         lat = np.array([r["end_ms"] - r["submit_ms"] for r in done])
         acc = int(sum(int(r["counts"][:, 1].sum()) for r in done))
         span_ms = (max(r["end_ms"] for r in done) - min(r["submit_ms"] for r in done)) if done else 0.0
-        return {"jobs": len(ids), "completed": len(done), "failed": sum(1 for r in res.values() if r["state"] != 0),
+        failed = [(r["state"], r["shots"]) for r in res.values() if r["state"] != 0]
+        return {"jobs": len(ids), "completed": len(done), "failed": len(failed), "failures": failed[:8],
                 "arrival_rate_per_s": rate, "window_s": duration_s,
                 "p50_job_ms": float(np.percentile(lat, 50)) if len(lat) else None,
                 "p99_job_ms": float(np.percentile(lat, 99)) if len(lat) else None,

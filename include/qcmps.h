@@ -71,7 +71,8 @@ typedef struct {
     int64_t n_decided;       /* measurements decided by stabiliser tracking (Sec. 4.2) */
     int64_t n_resets;
     int64_t n_t;             /* T and T^dagger gates */
-    int64_t n_mps_updates;   /* two-site updates per shot after SWAP routing and centre moves */
+    int64_t n_mps_updates;   /* two-site updates and centre moves per shot after SWAP routing */
+    int64_t n_product_swaps; /* routing SWAPs with an unentangled qubit: exact, no decomposition */
 } qc_circuit_info;
 
 /* Parse circuit text (len bytes, need not be NUL-terminated).  Runs the offline analysis of

@@ -25,7 +25,8 @@ class QcError(RuntimeError):
 class CircuitInfo(C.Structure):
     _fields_ = [("n_qubits", C.c_int32), ("n_ops", C.c_int64), ("n_channels", C.c_int64),
                 ("n_measurements", C.c_int64), ("n_decided", C.c_int64), ("n_resets", C.c_int64),
-                ("n_t", C.c_int64), ("n_mps_updates", C.c_int64)]
+                ("n_t", C.c_int64), ("n_mps_updates", C.c_int64),
+                ("n_product_swaps", C.c_int64)]
 
 
 class Noise(C.Structure):

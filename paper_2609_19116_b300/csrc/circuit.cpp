@@ -190,43 +190,86 @@ static uint32_t g1_index(uint8_t k) {
     }
 }
 
-// Execution order of the instructions for the MPS engine.  Instructions on disjoint qubits
-// commute, so the order may follow the orthogonality centre instead of the text: a greedy list
-// schedule over the dependency graph (each qubit's instructions stay in text order) that always
-// takes the ready instruction closest to the current centre.  Readouts (M and R) also stay in text
-// order among themselves, so every readout sees the same earlier projections as in text order
-// and a shot's sampled outcomes do not depend on the schedule.
-static std::vector<size_t> schedule_ops(const CircuitImpl& c) {
+// Execution order and SWAP routing of the instructions for the MPS engine.
+//
+// Order.  Instructions on disjoint qubits commute, so the order may follow the orthogonality
+// centre instead of the text: a greedy list schedule over the dependency graph (each qubit's
+// instructions stay in text order) that always takes the ready instruction closest to the centre.
+// Readouts (M and R) also stay in text order among themselves, so every readout sees the same
+// earlier projections as in text order and a shot's sampled outcomes do not depend on the schedule.
+//
+// Routing (Sec. 3.1: gates between qubits that are not neighbours on the line go through SWAPs).
+// The line holds a permutation of the logical qubits.  A two-qubit gate at line distance d > 1
+// moves one of its qubits next to the other with d - 1 adjacent SWAPs and leaves it there instead
+// of swapping it back.  The qubit that moves is, in this order: the one in a product state (its
+// SWAPs need no decomposition, see below); the one whose next reset comes first (an ancilla, which
+// walks home after that reset); the one whose next partner lies closer to where it would land.
+// A logical SWAP gate only exchanges the two labels.
+//
+// Product states are known at compile time: a qubit is unentangled from its last readout (which
+// leaves it in |0>) or from the start until its next entangling gate, since single-qubit gates and
+// Pauli faults keep it so.  Its site tensor is then |0> x M with the single-qubit gates since the
+// readout still pending, and a SWAP with it is a relabelling of bonds (M_PSWAP), exact and cheap.
+// After a reset the qubit walks back to its home site that way.
+static void compile_mps(CircuitImpl& c) {
     const size_t N = c.ops.size();
+    const int n = c.n;
+    // dependency graph
     std::vector<std::vector<uint32_t>> succ(N);
     std::vector<int> indeg(N, 0);
-    std::vector<long> last_q(c.n, -1);
-    long last_read = -1;
+    {
+        std::vector<long> last_q(n, -1);
+        long last_read = -1;
+        for (size_t i = 0; i < N; ++i) {
+            const Op& op = c.ops[i];
+            long deps[3] = {last_q[op.q0], op.q1 >= 0 ? last_q[op.q1] : -1,
+                            (op.kind == K_M || op.kind == K_R) ? last_read : -1};
+            for (int a = 0; a < 3; ++a) {
+                if (deps[a] < 0) continue;
+                bool dup = false;
+                for (int b = 0; b < a; ++b) dup |= deps[b] == deps[a];
+                if (dup) continue;
+                succ[deps[a]].push_back((uint32_t)i);
+                ++indeg[i];
+            }
+            last_q[op.q0] = (long)i;
+            if (op.q1 >= 0) last_q[op.q1] = (long)i;
+            if (op.kind == K_M || op.kind == K_R) last_read = (long)i;
+        }
+    }
+    // per qubit, text positions of its resets and of its two-qubit gates (for the mover choice)
+    std::vector<std::vector<uint32_t>> resets(n), gates2(n);
     for (size_t i = 0; i < N; ++i) {
         const Op& op = c.ops[i];
-        long deps[3] = {last_q[op.q0], op.q1 >= 0 ? last_q[op.q1] : -1,
-                        (op.kind == K_M || op.kind == K_R) ? last_read : -1};
-        for (int a = 0; a < 3; ++a) {
-            if (deps[a] < 0) continue;
-            bool dup = false;
-            for (int b = 0; b < a; ++b) dup |= deps[b] == deps[a];
-            if (dup) continue;
-            succ[deps[a]].push_back((uint32_t)i);
-            ++indeg[i];
+        if (op.kind == K_R) resets[op.q0].push_back((uint32_t)i);
+        if (op.kind == K_CX || op.kind == K_CZ || op.kind == K_SWAP) {
+            gates2[op.q0].push_back((uint32_t)i);
+            gates2[op.q1].push_back((uint32_t)i);
         }
-        last_q[op.q0] = (long)i;
-        if (op.q1 >= 0) last_q[op.q1] = (long)i;
-        if (op.kind == K_M || op.kind == K_R) last_read = (long)i;
     }
+    auto next_after = [](const std::vector<uint32_t>& v, size_t i) -> long {
+        auto it = std::upper_bound(v.begin(), v.end(), (uint32_t)i);
+        return it == v.end() ? -1 : (long)*it;
+    };
+    std::vector<int> pos(n), at(n);
+    std::vector<char> prod(n, 1);
+    for (int q = 0; q < n; ++q) pos[q] = at[q] = q;
+
+    std::vector<SiteOp> s;
+    auto emit_swap = [&](int k) {  // exchange the qubits on sites k and k+1
+        const int x = at[k], y = at[k + 1];
+        if (prod[x] || prod[y]) s.push_back({M_PSWAP, (uint8_t)(prod[x] ? F_PROD_LEFT : 0), k, 0, 0, -1});
+        else s.push_back({M_G2, 0, k, G4_SWAP, 0, -1});
+        at[k] = y; at[k + 1] = x;
+        pos[x] = k + 1; pos[y] = k;
+    };
+    auto needs_center = [&](const Op& op) {
+        return op.kind == K_CX || op.kind == K_CZ || op.kind == K_M || op.kind == K_R;
+    };
     std::vector<uint32_t> ready;
     for (size_t i = 0; i < N; ++i)
         if (indeg[i] == 0) ready.push_back((uint32_t)i);
-    std::vector<size_t> order;
-    order.reserve(N);
     int center = 0;
-    auto needs_center = [&](const Op& op) {
-        return op.kind == K_CX || op.kind == K_CZ || op.kind == K_SWAP || op.kind == K_M || op.kind == K_R;
-    };
     while (!ready.empty()) {
         // instructions that need no centre go first (lowest text index), else the nearest one
         size_t best = 0;
@@ -235,8 +278,8 @@ static std::vector<size_t> schedule_ops(const CircuitImpl& c) {
             const Op& op = c.ops[ready[k]];
             long dist = 0;
             if (needs_center(op)) {
-                const int lo = op.q1 >= 0 ? std::min(op.q0, op.q1) : op.q0;
-                const int hi = op.q1 >= 0 ? std::max(op.q0, op.q1) : op.q0;
+                const int p0 = pos[op.q0], p1 = op.q1 >= 0 ? pos[op.q1] : p0;
+                const int lo = std::min(p0, p1), hi = std::max(p0, p1);
                 dist = 1 + (center < lo ? lo - center : center > hi ? center - hi : 0);
             }
             const long key = dist * (long)(N + 1) + (long)ready[k];
@@ -245,62 +288,92 @@ static std::vector<size_t> schedule_ops(const CircuitImpl& c) {
         const uint32_t i = ready[best];
         ready[best] = ready.back();
         ready.pop_back();
-        order.push_back(i);
         const Op& op = c.ops[i];
+        const int32_t src = (int32_t)i;
+        switch (op.kind) {
+            case K_H: case K_S: case K_SDG: case K_X: case K_Y: case K_Z: case K_T: case K_TDG:
+                s.push_back({M_G1, 0, pos[op.q0], g1_index(op.kind), 0, src});
+                break;
+            case K_SWAP: {  // relabel
+                const int a = op.q0, b = op.q1;
+                std::swap(pos[a], pos[b]);
+                at[pos[a]] = a;
+                at[pos[b]] = b;
+                std::swap(prod[a], prod[b]);
+                break;
+            }
+            case K_CX: case K_CZ: {
+                const int a = op.q0, b = op.q1;
+                int mv;
+                if (prod[a] != prod[b]) {
+                    mv = prod[a] ? a : b;
+                } else {
+                    const long ra = next_after(resets[a], i), rb = next_after(resets[b], i);
+                    if (ra != rb && (ra >= 0 || rb >= 0)) {
+                        mv = (rb < 0 || (ra >= 0 && ra < rb)) ? a : b;
+                    } else {
+                        auto score = [&](int m_, int o_) {
+                            const int d = std::abs(pos[m_] - pos[o_]) - 1;
+                            const int dest = pos[m_] < pos[o_] ? pos[o_] - 1 : pos[o_] + 1;
+                            double sc = d;
+                            const long j = next_after(gates2[m_], i);
+                            if (j >= 0) {
+                                const Op& nx = c.ops[j];
+                                const int partner = nx.q0 == m_ ? nx.q1 : nx.q0;
+                                if (partner != o_) sc += 0.5 * std::max(0, std::abs(dest - pos[partner]) - 1);
+                            }
+                            return sc;
+                        };
+                        mv = score(a, b) <= score(b, a) ? a : b;
+                    }
+                }
+                const int other = mv == a ? b : a;
+                while (std::abs(pos[mv] - pos[other]) > 1) emit_swap(pos[mv] < pos[other] ? pos[mv] : pos[mv] - 1);
+                const int left = std::min(pos[a], pos[b]);
+                uint32_t g;
+                if (op.kind == K_CX) g = (pos[a] == left) ? G4_CX_HL : G4_CX_LH;
+                else g = G4_CZ;
+                s.push_back({M_G2, 0, left, g, 0, src});
+                prod[a] = prod[b] = 0;
+                break;
+            }
+            case K_DEP1: s.push_back({M_CH1, 0, pos[op.q0], op.aux, 0, src}); break;
+            case K_XERR: s.push_back({M_CH1, F_XERR, pos[op.q0], op.aux, 0, src}); break;
+            case K_DEP2: s.push_back({M_CH2, 0, pos[op.q0], op.aux, (uint32_t)pos[op.q1], src}); break;
+            case K_M:
+                s.push_back({M_MEAS, F_POSTSELECT, pos[op.q0], op.aux, 0, src});
+                prod[op.q0] = 1;
+                break;
+            case K_R: {
+                const int q = op.q0;
+                s.push_back({M_RESET, 0, pos[q], op.aux, 0, src});
+                prod[q] = 1;
+                while (pos[q] != q) emit_swap(pos[q] > q ? pos[q] - 1 : pos[q]);
+                break;
+            }
+            default: break;
+        }
         if (needs_center(op)) {
-            const int lo = op.q1 >= 0 ? std::min(op.q0, op.q1) : op.q0;
-            const int hi = op.q1 >= 0 ? std::max(op.q0, op.q1) : op.q0;
+            const int p0 = pos[op.q0], p1 = op.q1 >= 0 ? pos[op.q1] : p0;
+            const int lo = std::min(p0, p1), hi = std::max(p0, p1);
             center = center < lo ? lo : (center > hi ? hi : center);
         }
         for (uint32_t sx : succ[i])
             if (--indeg[sx] == 0) ready.push_back(sx);
     }
-    return order;
-}
 
-static void compile_mps(CircuitImpl& c) {
-    // 1. expand into site operations with SWAP routing (Sec. 3.1), in the scheduled order.
-    std::vector<SiteOp> s;
-    const std::vector<size_t> order = schedule_ops(c);
-    for (size_t i : order) {
-        const Op& op = c.ops[i];
-        const int32_t src = (int32_t)i;
-        switch (op.kind) {
-            case K_H: case K_S: case K_SDG: case K_X: case K_Y: case K_Z: case K_T: case K_TDG:
-                s.push_back({M_G1, 0, op.q0, g1_index(op.kind), 0, src});
-                break;
-            case K_CX: case K_CZ: case K_SWAP: {
-                const int a = op.q0, b = op.q1;
-                const int lo = a < b ? a : b, hi = a < b ? b : a;
-                for (int k = lo; k < hi - 1; ++k) s.push_back({M_G2, 0, k, G4_SWAP, 0, -1});
-                // after routing the qubit from `lo` sits at hi-1 (high bit of the pair)
-                uint32_t g;
-                if (op.kind == K_CX) g = (a == lo) ? G4_CX_HL : G4_CX_LH;
-                else if (op.kind == K_CZ) g = G4_CZ;
-                else g = G4_SWAP;
-                s.push_back({M_G2, 0, hi - 1, g, 0, src});
-                for (int k = hi - 2; k >= lo; --k) s.push_back({M_G2, 0, k, G4_SWAP, 0, -1});
-                break;
-            }
-            case K_DEP1: s.push_back({M_CH1, 0, op.q0, op.aux, 0, src}); break;
-            case K_XERR: s.push_back({M_CH1, F_XERR, op.q0, op.aux, 0, src}); break;
-            case K_DEP2: s.push_back({M_CH2, 0, op.q0, op.aux, (uint32_t)op.q1, src}); break;
-            case K_M: s.push_back({M_MEAS, F_POSTSELECT, op.q0, op.aux, 0, src}); break;
-            case K_R: s.push_back({M_RESET, 0, op.q0, op.aux, 0, src}); break;
-            default: break;
-        }
-    }
-    // 2. centre planning: each G2 needs the centre on one of its sites, each readout on its site;
-    //    after a G2 the centre goes to the side of the next site that needs it.
-    const size_t N = s.size();
-    std::vector<int> next_need(N + 1, -1);  // position (site) of the next centre-needing op
-    for (size_t i = N; i-- > 0;) {
+    // centre planning: each G2 needs the centre on one of its sites, each readout on its site;
+    // after a G2 the centre goes to the side of the next site that needs it.  A product SWAP needs
+    // no centre; when the centre is on its pair it ends on the entangled qubit's new site.
+    const size_t NS = s.size();
+    std::vector<int> next_need(NS + 1, -1);  // position (site) of the next centre-needing op
+    for (size_t i = NS; i-- > 0;) {
         next_need[i] = next_need[i + 1];
         if (s[i].kind == M_G2) next_need[i] = s[i].q;  // pair (q, q+1)
         else if (s[i].kind == M_MEAS || s[i].kind == M_RESET) next_need[i] = s[i].q;
     }
     c.mps.clear();
-    int center = 0;
+    center = 0;
     auto move_to = [&](int t) {
         while (center < t) {
             c.mps.push_back({M_MOVE, F_CENTER_RIGHT, (uint16_t)center, 0, 0, -1});
@@ -311,7 +384,7 @@ static void compile_mps(CircuitImpl& c) {
             --center;
         }
     };
-    for (size_t i = 0; i < N; ++i) {
+    for (size_t i = 0; i < NS; ++i) {
         const SiteOp& o = s[i];
         if (o.kind == M_G2) {
             if (center < o.q) move_to(o.q);
@@ -320,6 +393,9 @@ static void compile_mps(CircuitImpl& c) {
             const bool right = (nx < 0) ? true : (nx > o.q);
             c.mps.push_back({M_G2, (uint8_t)(right ? F_CENTER_RIGHT : 0), (uint16_t)o.q, o.a, 0, o.src});
             center = right ? o.q + 1 : o.q;
+        } else if (o.kind == M_PSWAP) {
+            c.mps.push_back({M_PSWAP, o.flags, (uint16_t)o.q, 0, 0, -1});
+            if (center == o.q || center == o.q + 1) center = (o.flags & F_PROD_LEFT) ? o.q : o.q + 1;
         } else if (o.kind == M_MEAS || o.kind == M_RESET) {
             move_to(o.q);
             c.mps.push_back({o.kind, o.flags, (uint16_t)o.q, o.a, 0, o.src});
@@ -328,7 +404,11 @@ static void compile_mps(CircuitImpl& c) {
         }
     }
     c.n_updates = 0;
-    for (const MpsOp& m : c.mps) c.n_updates += (m.kind == M_G2 || m.kind == M_MOVE);
+    c.n_pswaps = 0;
+    for (const MpsOp& m : c.mps) {
+        c.n_updates += (m.kind == M_G2 || m.kind == M_MOVE);
+        c.n_pswaps += m.kind == M_PSWAP;
+    }
 }
 
 CircuitImpl::~CircuitImpl() {
@@ -468,6 +548,7 @@ extern "C" qc_status qc_circuit_get_info(const qc_circuit* circuit, qc_circuit_i
     out->n_resets = c.n_resets;
     out->n_t = c.n_t;
     out->n_mps_updates = c.n_updates;
+    out->n_product_swaps = c.n_pswaps;
     return QC_OK;
 }
 

@@ -229,6 +229,12 @@ struct Engine {
         bsync<NT>();
     }
 
+    // Sum over the block in the working precision (identical on every thread).
+    __device__ R sum_r(R v) {
+        if (NT == 32) return warp_sum<R>(v);
+        return (R)block_sum<NT>((double)v, S.red, tid_);
+    }
+
     // ---- one-sided Jacobi on the columns of X (rows x cols, leading dimension ld) ---------------
     // Round-robin ordering: n-1 rounds of n/2 disjoint column pairs.  The pairs of a round are
     // spread over the warps, and within a warp over lane groups of g lanes (g = 32 / pairs per warp,
@@ -236,8 +242,8 @@ struct Engine {
     // Pairs whose smaller column is below the numerical floor are left alone: such a column is
     // rounding noise of a rank-deficient theta, and rotating it against a large column never
     // reaches relative orthogonality.
-    __device__ bool jacobi(V* X, int rows, int cols, int ld, R floor2, V* Vm = nullptr, int vdim = 0,
-                           int max_sweeps = 0, int* any_rotation = nullptr) {
+    __device__ bool jacobi(V* X, int rows, int cols, int ld, R floor2, int max_sweeps = 0,
+                           int* any_rotation = nullptr) {
         const int lane = tid_ & 31, wid = tid_ >> 5;
         constexpr int NW = NT / 32;
         const R eps = sizeof(R) == 4 ? (R)FLT_EPSILON : (R)DBL_EPSILON;
@@ -290,17 +296,6 @@ struct Engine {
                             a[i] = cmk<V>(c * x.x - sn * emx, c * x.y - sn * emy);
                             b[i] = cmk<V>(sn * epx + c * y.x, sn * epy + c * y.y);
                         }
-                        if (Vm) {  // the same rotation on the accumulated right factor (vdim x vdim)
-                            V* va = Vm + (size_t)ca * vdim;
-                            V* vb = Vm + (size_t)cb * vdim;
-                            for (int i = gl; i < vdim; i += g) {
-                                const V x = va[i], y = vb[i];
-                                const R emx = er * y.x + ei * y.y, emy = er * y.y - ei * y.x;
-                                const R epx = er * x.x - ei * x.y, epy = er * x.y + ei * x.x;
-                                va[i] = cmk<V>(c * x.x - sn * emx, c * x.y - sn * emy);
-                                vb[i] = cmk<V>(sn * epx + c * y.x, sn * epy + c * y.y);
-                            }
-                        }
                     }
                 }
                 bsync<NT>();
@@ -342,7 +337,7 @@ struct Engine {
                         W[(size_t)c * lw + i] = v;
                     }
                     bsync<NT>();
-                    jacobi(W, rows, ncp, lw, floor2, nullptr, 0, 3, &rot);
+                    jacobi(W, rows, ncp, lw, floor2, 3, &rot);
                     for (int e = tid_; e < nc * rows; e += NT) {
                         const int c = e / rows, i = e - c * rows;
                         const V v = W[(size_t)c * lw + i];
@@ -501,7 +496,7 @@ struct Engine {
         if (tid_ == 0) { reset_pend(q); reset_pend(q + 1); }
         const V* gt = S.gate;
         // theta'[(l,s),(t,r)] = sum_{s',t'} gate[(s,t),(s',t')] sum_k A[l,s',k] B[k,t',r]
-        double fro = 0;
+        R fro = 0;  // only sets the numerical floor: the working precision suffices
         for (int e = tid_; e < cl * cr; e += NT) {
             const int l = e / cr, r = e - l * cr;
             V th[4];
@@ -523,7 +518,7 @@ struct Engine {
 #pragma unroll
                 for (int u = 0; u < 4; ++u) v = cfma(gt[st * 4 + u], th[u], v);
                 const int i = l * 2 + (st >> 1), j = (st & 1) * cr + r;
-                fro += (double)v.x * v.x + (double)v.y * v.y;
+                fro = fma(v.x, v.x, fma(v.y, v.y, fro));
                 if (!fast) T[(size_t)i * n + j] = v;
                 if (right) X[(size_t)j * ld + i] = v;
                 else X[(size_t)i * ld + j] = cmk<V>(v.x, -v.y);
@@ -537,10 +532,10 @@ struct Engine {
                 T[e] = right ? v : cmk<V>(v.x, -v.y);
             }
         }
-        fro = block_sum<NT>(fro, S.red, tid_);
+        const double frod = block_sum<NT>((double)fro, S.red, tid_);
         const R eps = sizeof(R) == 4 ? (R)FLT_EPSILON : (R)DBL_EPSILON;
         const R fl = (R)4 * eps * sqrt((R)rows);
-        const R floor2 = fl * fl * (R)fro;
+        const R floor2 = fl * fl * (R)frod;
         const int bw = (int)(P.x_smem / (2 * (uint32_t)(rows + 1)));
         const bool blocked = (X == xg) && bw >= 2 && bw * 2 < cols;
         if (!(blocked ? jacobi_blocked(X, rows, cols, ld, floor2, S.X, bw) : jacobi(X, rows, cols, ld, floor2))) {
@@ -601,44 +596,105 @@ struct Engine {
         bsync<NT>();
         chi_peak = max(chi_peak, r);
         ++nupd;
-        {
+        if (tid_ == 0) {  // accounting in FP64 on one thread: the FP64 pipe is narrow on this part
             const double M = (double)max(m, n), Nn = (double)min(m, n);
             flops += 8.0 * m * cm * n + 128.0 * cl * cr + 4.0 * (4.0 * M * M * Nn + 22.0 * Nn * Nn * Nn) +
                      8.0 * r * m * n;
         }
     }
 
-    // ---- centre move between q and q+1 without a gate: split one site tensor ----------------------
-    // Right: one-sided Jacobi on the columns of A[q] (m x cm) with the rotations accumulated in V
-    // (cm x cm); A[q] V = U S gives A[q] = U and the centre S V^H A[q+1].  Left: the same on A[q+1]^H,
-    // A[q+1] = V S U'^H gives A[q+1] = U'^H and the centre A[q] V S.  The singular values equal
-    // those of the two-site theta (the neighbour is canonical), so the truncation rule applies as in
-    // a two-site update.
+    // ---- QR of X (rows x cols, leading dimension ld) by classical Gram-Schmidt -------------------
+    // Each column is orthogonalised against the kept ones, the pass repeated while it removes more
+    // than half of the column's squared norm (the Daniel-Gragg-Kaufman-Stewart test), so every kept
+    // column is orthogonal to the earlier ones to rounding.  A column whose remainder falls to the
+    // floor depends on the kept ones and is dropped.  On return the kept columns of X are
+    // orthonormal, perm[0..k) lists them in order, and Rm (row-major, k x cols, zeroed by the
+    // caller) holds R: X_in = Q R.  hb: scratch of cols elements.  Returns k.
+    __device__ int gram_schmidt(V* X, int rows, int cols, int ld, V* Rm, V* hb, int* perm, R floor2,
+                                double& dropped) {
+        int k = 0;
+        for (int j = 0; j < cols; ++j) {
+            V* x = X + (size_t)j * ld;
+            R part = 0;
+            for (int i = tid_; i < rows; i += NT) part = fma(x[i].x, x[i].x, fma(x[i].y, x[i].y, part));
+            R nold = sum_r(part), nnow = nold;
+            for (int pass = 0; pass < 4 && k > 0; ++pass) {
+                for (int i = tid_; i < k; i += NT) {  // h_i = <q_i, x>
+                    const V* qi = X + (size_t)perm[i] * ld;
+                    V h0 = cmk<V>(0, 0), h1 = cmk<V>(0, 0);
+                    int t = 0;
+                    for (; t + 1 < rows; t += 2) {
+                        h0 = cfmac(qi[t], x[t], h0);
+                        h1 = cfmac(qi[t + 1], x[t + 1], h1);
+                    }
+                    if (t < rows) h0 = cfmac(qi[t], x[t], h0);
+                    const V h = cmk<V>(h0.x + h1.x, h0.y + h1.y);
+                    hb[i] = h;
+                    V& rr = Rm[(size_t)i * cols + j];
+                    rr = cmk<V>(rr.x + h.x, rr.y + h.y);
+                }
+                bsync<NT>();
+                part = 0;
+                for (int t = tid_; t < rows; t += NT) {  // x -= sum_i h_i q_i
+                    V acc = x[t];
+                    for (int i = 0; i < k; ++i) {
+                        const V h = hb[i], u = X[(size_t)perm[i] * ld + t];
+                        acc = cmk<V>(acc.x - (h.x * u.x - h.y * u.y), acc.y - (h.x * u.y + h.y * u.x));
+                    }
+                    x[t] = acc;
+                    part = fma(acc.x, acc.x, fma(acc.y, acc.y, part));
+                }
+                bsync<NT>();
+                nnow = sum_r(part);
+                const bool done = nnow > (R)0.5 * nold;
+                nold = nnow;
+                if (done) break;
+            }
+            if (nnow > floor2) {
+                const R nr = sqrt(nnow), inv = (R)1 / nr;
+                for (int t = tid_; t < rows; t += NT) x[t] = cmk<V>(x[t].x * inv, x[t].y * inv);
+                if (tid_ == 0) {
+                    Rm[(size_t)k * cols + j] = cmk<V>(nr, (R)0);
+                    perm[k] = j;
+                }
+                ++k;
+            } else {
+                dropped += (double)nnow;
+            }
+            bsync<NT>();
+        }
+        return k;
+    }
+
+    // ---- centre move between q and q+1 without a gate: QR of one site tensor ---------------------
+    // Right: A[q] (m x cm) = Q R, A[q] = Q and the centre R A[q+1].  Left: the same on A[q+1]^H
+    // (n x cm); A[q+1] = R^H Q^H gives A[q+1] = Q^H and the centre A[q] R^H.  Columns at the
+    // numerical floor are dropped (gram_schmidt), so the bond shrinks to the numerical rank.
+    // Nothing else is truncated, so a move leaves the state as it was (Sec. 3.1: moving the
+    // orthogonality centre is a gauge change).
     __device__ void move(int q, bool right) {
         bsync<NT>();
         const int cl = S.dims[q], cm = S.dims[q + 1], cr = S.dims[q + 2];
         const int m = 2 * cl, n = 2 * cr;
-        // the round-robin ordering needs an even column count: an odd bond gets a zero column,
-        // which is never rotated and is dropped as numerically zero
-        const int rows = right ? m : n, cols = cm + (cm & 1);
+        const int rows = right ? m : n;
         const int ld = rows + 1;
         const uint64_t other = right ? (uint64_t)cm * n : (uint64_t)m * cm;
-        const uint64_t sgw = ((uint64_t)cols * (sizeof(R) + sizeof(int)) + sizeof(V) - 1) / sizeof(V);
-        const bool fast = (uint64_t)ld * cols + (uint64_t)cm * cm + other + sgw <= P.x_smem;
+        const uint64_t hw = (uint64_t)cm + ((uint64_t)cm * sizeof(int) + sizeof(V) - 1) / sizeof(V);
+        const bool fast = (uint64_t)ld * cm + (uint64_t)cm * cm + other + hw <= P.x_smem;
         V* X = fast ? S.X : xg;
-        V* Vm = X + (size_t)ld * cols;
-        V* O = fast ? Vm + (size_t)cm * cm : nullptr;  // staged copy of the other tensor
-        R* sig2 = fast ? reinterpret_cast<R*>(O + other) : gsig2;
-        int* perm = reinterpret_cast<int*>(sig2 + cols);
+        V* Rm = X + (size_t)ld * cm;                  // R, row-major: kept index x cm
+        V* O = fast ? Rm + (size_t)cm * cm : nullptr;  // staged copy of the other tensor
+        V* hb = fast ? O + other : reinterpret_cast<V*>(gsig2);  // one pass's projections
+        int* perm = reinterpret_cast<int*>(hb + cm);             // kept columns, in order
         V* A = site(q);
         V* B = site(q + 1);
-        double fro = 0;
+        R fro = 0;
         if (right) {
             for (int e = tid_; e < m * cm; e += NT) {
                 const int i = e / cm, j = e - i * cm;
                 const V v = A[e];
                 X[(size_t)j * ld + i] = v;
-                fro += (double)v.x * v.x + (double)v.y * v.y;
+                fro = fma(v.x, v.x, fma(v.y, v.y, fro));
             }
             if (fast) for (int e = tid_; e < cm * n; e += NT) O[e] = B[e];
         } else {
@@ -646,74 +702,54 @@ struct Engine {
                 const int k = e / n, j = e - k * n;
                 const V v = B[e];
                 X[(size_t)k * ld + j] = cmk<V>(v.x, -v.y);
-                fro += (double)v.x * v.x + (double)v.y * v.y;
+                fro = fma(v.x, v.x, fma(v.y, v.y, fro));
             }
             if (fast) for (int e = tid_; e < m * cm; e += NT) O[e] = A[e];
         }
-        for (int e = tid_; e < cm * cm; e += NT) {
-            const int a = e / cm, b = e - a * cm;
-            Vm[e] = cmk<V>(a == b ? (R)1 : (R)0, (R)0);
-        }
-        if (cols > cm)
-            for (int i = tid_; i < rows; i += NT) X[(size_t)cm * ld + i] = cmk<V>(0, 0);
+        for (int e = tid_; e < cm * cm; e += NT) Rm[e] = cmk<V>(0, 0);
         const V* Bo = right ? (fast ? O : B) : B;
         const V* Ao = right ? A : (fast ? O : A);
-        fro = block_sum<NT>(fro, S.red, tid_);
+        const double frod = block_sum<NT>((double)fro, S.red, tid_);
         const R eps = sizeof(R) == 4 ? (R)FLT_EPSILON : (R)DBL_EPSILON;
         const R fl = (R)4 * eps * sqrt((R)rows);
-        const R floor2 = fl * fl * (R)fro;
-        if (!jacobi(X, rows, cols, ld, floor2, Vm, cm)) {
+        const R floor2 = fl * fl * (R)frod;
+        bsync<NT>();
+        double dropped = 0;
+        const int k = gram_schmidt(X, rows, cm, ld, Rm, hb, perm, floor2, dropped);
+        const int r = k;
+        if (r == 0) {  // a site tensor at the numerical floor: the state has lost its norm
             status = QC_ENOCONV;
             return;
         }
-        const int r = spectrum(X, rows, cols, ld, sig2, perm, floor2);
-        const R scale = (R)S.red[41];
-        if (r > P.cap[q + 1]) {
-            status = QC_ECAPACITY;
-            return;
-        }
-        for (int e = tid_; e < r * rows; e += NT) {  // the orthonormal factor
-            const int k = e / rows, i = e - k * rows;
-            const R sg = sig2[perm[k]];
-            const R inv = sg > (R)0 ? (R)1 / sqrt(sg) : (R)0;
-            V* col = X + (size_t)perm[k] * ld;
-            col[i] = cmk<V>(col[i].x * inv, col[i].y * inv);
-        }
-        bsync<NT>();
+        if (frod > 0) disc += dropped / frod;
         if (right) {
-            // A[q] = U (cl, 2, r);  A[q+1] = scale S V^H B (r, 2, cr)
+            // A[q] = Q (cl, 2, r);  A[q+1] = R B (r, 2, cr), R upper triangular in column order
             for (int e = tid_; e < r * n; e += NT) {
-                const int kk = e / n, j = e - kk * n;
-                const int pc = perm[kk];
-                const V* v = Vm + (size_t)pc * cm;
+                const int kk = e / n, jn = e - kk * n;
+                const V* rrow = Rm + (size_t)kk * cm;
                 V acc = cmk<V>(0, 0);
-                if (pc < cm)  // the padding column is zero
-                    for (int k = 0; k < cm; ++k) acc = cfmac(v[k], Bo[(size_t)k * n + j], acc);
-                const R f = scale * sqrt(sig2[pc]);
-                tcopy[e] = cmk<V>(acc.x * f, acc.y * f);
+                for (int j = perm[kk]; j < cm; ++j) acc = cfma(rrow[j], Bo[(size_t)j * n + jn], acc);
+                tcopy[e] = acc;
             }
             bsync<NT>();
             for (int e = tid_; e < m * r; e += NT) {
-                const int i = e / r, k = e - i * r;
-                A[e] = X[(size_t)perm[k] * ld + i];
+                const int i = e / r, kk = e - i * r;
+                A[e] = X[(size_t)perm[kk] * ld + i];
             }
             for (int e = tid_; e < r * n; e += NT) B[e] = tcopy[e];
         } else {
-            // A[q+1] = U'^H (r, 2, cr);  A[q] = scale A V S (cl, 2, r)
+            // A[q+1] = Q^H (r, 2, cr);  A[q] = A[q] R^H (cl, 2, r)
             for (int e = tid_; e < m * r; e += NT) {
                 const int i = e / r, kk = e - i * r;
-                const int pc = perm[kk];
-                const V* v = Vm + (size_t)pc * cm;
+                const V* rrow = Rm + (size_t)kk * cm;
                 V acc = cmk<V>(0, 0);
-                if (pc < cm)
-                    for (int k = 0; k < cm; ++k) acc = cfma(Ao[(size_t)i * cm + k], v[k], acc);
-                const R f = scale * sqrt(sig2[pc]);
-                tcopy[e] = cmk<V>(acc.x * f, acc.y * f);
+                for (int j = perm[kk]; j < cm; ++j) acc = cfmac(rrow[j], Ao[(size_t)i * cm + j], acc);
+                tcopy[e] = acc;
             }
             bsync<NT>();
             for (int e = tid_; e < r * n; e += NT) {
-                const int k = e / n, j = e - k * n;
-                const V u = X[(size_t)perm[k] * ld + j];
+                const int kk = e / n, jn = e - kk * n;
+                const V u = X[(size_t)perm[kk] * ld + jn];
                 B[e] = cmk<V>(u.x, -u.y);
             }
             for (int e = tid_; e < m * r; e += NT) A[e] = tcopy[e];
@@ -722,10 +758,150 @@ struct Engine {
         if (tid_ == 0) S.dims[q + 1] = r;
         bsync<NT>();
         ++nupd;
-        {
-            const double M = (double)max(rows, cols), Nn = (double)min(rows, cols);
-            flops += 4.0 * (4.0 * M * M * Nn + 22.0 * Nn * Nn * Nn) + 8.0 * r * cm * (right ? n : m);
+        if (tid_ == 0) {  // Householder QR count of the rows x cm factor, plus the product with R
+            const double M = (double)max(rows, cm), K = (double)min(rows, cm);
+            flops += 8.0 * (M * K * K - K * K * K / 3.0) + 8.0 * r * cm * (right ? n : m);
         }
+    }
+
+    // ---- SWAP with a qubit in a product state: a relabelling of bonds, no decomposition ---------
+    // The unentangled qubit's tensor is |0> x M: its last readout left slice 1 at exactly zero, and
+    // every single-qubit gate since then is still pending.  Product on the left (site q):
+    // C = M A[q+1] (cl, 2, cr) goes to site q and |0> x I (cr, 2, cr) to site q+1.  Product on the
+    // right: C = A[q] N (cl, 2, cr) goes to site q+1 and |0> x I (cl, 2, cl) to site q.  |0> x I is
+    // an isometry either way, so the canonical form holds; a centre on the pair ends on the
+    // entangled qubit's new site.  Pending gates travel with their qubits.
+    // A readout can leave a bond wider than the state needs (the projection is not followed by a
+    // split); when the new bond would exceed the rank bound of the other side (2 cl, resp. 2 cr) or
+    // the bond capacity, C is factorised instead (LQ, resp. QR, by Gram-Schmidt) with the
+    // orthonormal factor on the product qubit's new site, which keeps the canonical form.
+    __device__ void pswap(int q, bool prod_left) {
+        bsync<NT>();
+        const int cl = S.dims[q], cm = S.dims[q + 1], cr = S.dims[q + 2];
+        V* A = site(q);
+        V* B = site(q + 1);
+        const int n = 2 * cr;
+        R fro = 0;
+        if (prod_left) {
+            for (int e = tid_; e < cl * n; e += NT) {  // C(l, t, r) = sum_m A(l, 0, m) B(m, t, r)
+                const int l = e / n, j = e - l * n;
+                const V* arow = A + (size_t)(2 * l) * cm;
+                V acc = cmk<V>(0, 0);
+                for (int k = 0; k < cm; ++k) acc = cfma(arow[k], B[(size_t)k * n + j], acc);
+                tcopy[e] = acc;
+                fro = fma(acc.x, acc.x, fma(acc.y, acc.y, fro));
+            }
+        } else {
+            for (int e = tid_; e < 2 * cl * cr; e += NT) {  // C(l, s, r) = sum_m A(l, s, m) B(m, 0, r)
+                const int i = e / cr, r = e - i * cr;
+                const V* arow = A + (size_t)i * cm;
+                V acc = cmk<V>(0, 0);
+                for (int k = 0; k < cm; ++k) acc = cfma(arow[k], B[(size_t)(2 * k) * cr + r], acc);
+                tcopy[e] = acc;
+                fro = fma(acc.x, acc.x, fma(acc.y, acc.y, fro));
+            }
+        }
+        bsync<NT>();
+        int nb = prod_left ? cr : cl;  // the new bond between q and q+1
+        if (nb <= (prod_left ? 2 * cl : 2 * cr) && nb <= P.cap[q + 1]) {
+            if (prod_left) {
+                for (int e = tid_; e < cl * n; e += NT) A[e] = tcopy[e];
+                for (int e = tid_; e < cr * n; e += NT) {
+                    const int r1 = e / n, rem = e - r1 * n;
+                    B[e] = cmk<V>(rem == r1 ? (R)1 : (R)0, (R)0);  // (r1, s = 0, r2 = r1)
+                }
+            } else {
+                for (int e = tid_; e < 2 * cl * cr; e += NT) B[e] = tcopy[e];
+                for (int e = tid_; e < cl * 2 * cl; e += NT) {
+                    const int l1 = e / (2 * cl), rem = e - l1 * 2 * cl;
+                    A[e] = cmk<V>(rem == l1 ? (R)1 : (R)0, (R)0);  // (l1, s = 0, l2 = l1)
+                }
+            }
+        } else {
+            // left: C as (2cl) x cr = L Q', by QR of C^H (cr x 2cl);  right: C as cl x (2cr) = Q R
+            const int rows = prod_left ? cr : cl, cols = prod_left ? 2 * cl : 2 * cr;
+            const int ld = rows + 1;
+            const uint64_t hw = (uint64_t)cols + ((uint64_t)cols * sizeof(int) + sizeof(V) - 1) / sizeof(V);
+            const uint64_t need = (uint64_t)ld * cols + (uint64_t)cols * cols;
+            const bool fast = need + hw <= P.x_smem;
+            const uint64_t sg_bytes = (uint64_t)(2 * P.chi_max) * (sizeof(R) + sizeof(int));
+            if (!fast && (need > P.xg_elems || hw * sizeof(V) > sg_bytes)) {
+                status = QC_ECAPACITY;
+                return;
+            }
+            V* X = fast ? S.X : xg;
+            V* Rm = X + (size_t)ld * cols;
+            V* hb = fast ? Rm + (size_t)cols * cols : reinterpret_cast<V*>(gsig2);
+            int* perm = reinterpret_cast<int*>(hb + cols);
+            for (int e = tid_; e < rows * cols; e += NT) {
+                if (prod_left) {  // X[r, j] = conj C[j, r]
+                    const int j = e / cr, r = e - j * cr;
+                    const V c = tcopy[e];
+                    X[(size_t)j * ld + r] = cmk<V>(c.x, -c.y);
+                } else {          // X[l, j] = C[l, j]
+                    const int l = e / cols, j = e - l * cols;
+                    X[(size_t)j * ld + l] = tcopy[e];
+                }
+            }
+            for (int e = tid_; e < cols * cols; e += NT) Rm[e] = cmk<V>(0, 0);
+            const double frod = block_sum<NT>((double)fro, S.red, tid_);
+            const R eps = sizeof(R) == 4 ? (R)FLT_EPSILON : (R)DBL_EPSILON;
+            const R fl = (R)4 * eps * sqrt((R)rows);
+            const R floor2 = fl * fl * (R)frod;
+            bsync<NT>();
+            double dropped = 0;
+            const int k = gram_schmidt(X, rows, cols, ld, Rm, hb, perm, floor2, dropped);
+            if (k == 0) {
+                status = QC_ENOCONV;
+                return;
+            }
+            if (k > P.cap[q + 1]) {
+                status = QC_ECAPACITY;
+                return;
+            }
+            if (frod > 0) disc += dropped / frod;
+            nb = k;
+            if (prod_left) {
+                // A[q](l, t, kk) = conj R[kk, (l, t)];  A[q+1](kk, s, r) = [s = 0] conj Q[r, kk]
+                for (int e = tid_; e < cols * k; e += NT) {
+                    const int j = e / k, kk = e - j * k;
+                    const V u = Rm[(size_t)kk * cols + j];
+                    A[e] = cmk<V>(u.x, -u.y);
+                }
+                for (int e = tid_; e < k * n; e += NT) {
+                    const int kk = e / n, rem = e - kk * n;
+                    V v = cmk<V>(0, 0);
+                    if (rem < cr) {
+                        const V u = X[(size_t)perm[kk] * ld + rem];
+                        v = cmk<V>(u.x, -u.y);
+                    }
+                    B[e] = v;
+                }
+            } else {
+                // A[q](l, t, kk) = [t = 0] Q[l, kk];  A[q+1](kk, s, r) = R[kk, (s, r)]
+                for (int e = tid_; e < cl * 2 * k; e += NT) {
+                    const int l = e / (2 * k), rem = e - l * 2 * k;
+                    A[e] = rem < k ? X[(size_t)perm[rem] * ld + l] : cmk<V>(0, 0);
+                }
+                for (int e = tid_; e < k * cols; e += NT) B[e] = Rm[e];
+            }
+            if (tid_ == 0) {
+                const double M = (double)max(rows, cols), K = (double)min(rows, cols);
+                flops += 8.0 * (M * K * K - K * K * K / 3.0);
+            }
+        }
+        bsync<NT>();
+        if (tid_ == 0) {
+            S.dims[q + 1] = nb;
+            for (int k = 0; k < 4; ++k) {
+                const V t = S.pend[q * 4 + k];
+                S.pend[q * 4 + k] = S.pend[(q + 1) * 4 + k];
+                S.pend[(q + 1) * 4 + k] = t;
+            }
+            flops += 16.0 * cl * cm * cr;
+        }
+        bsync<NT>();
+        chi_peak = max(chi_peak, nb);
     }
 
     // ---- readout on site q (the orthogonality centre) ------------------------------------------
@@ -952,6 +1128,9 @@ struct Engine {
                         break;
                     case M_MOVE:
                         move(op.q, (op.flags & F_CENTER_RIGHT) != 0);
+                        break;
+                    case M_PSWAP:
+                        pswap(op.q, (op.flags & F_PROD_LEFT) != 0);
                         break;
                     case M_MEAS:
                     case M_RESET:
@@ -1361,7 +1540,10 @@ static qc_status run_engine(CircuitImpl& c, qc_noise noise, const uint64_t* shot
         int center = 0;
         for (const MpsOp& o : c.mps) {
             if (o.kind == M_G2) center = (o.flags & F_CENTER_RIGHT) ? o.q + 1 : o.q;
+            else if (o.kind == M_MOVE) center = (o.flags & F_CENTER_RIGHT) ? o.q + 1 : o.q;
             else if (o.kind == M_MEAS || o.kind == M_RESET) center = o.q;
+            else if (o.kind == M_PSWAP && (center == o.q || center == o.q + 1))
+                center = (o.flags & F_PROD_LEFT) ? o.q : o.q + 1;
         }
         P.final_center = center;
     }

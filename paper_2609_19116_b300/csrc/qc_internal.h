@@ -35,8 +35,9 @@ inline PreOp make_preop(uint32_t kind, uint32_t q0, uint32_t q1, uint32_t chan) 
 }
 
 // ---- MPS program ---------------------------------------------------------------------------
-enum MpsKind : uint8_t { M_G1 = 0, M_G2, M_CH1, M_CH2, M_MEAS, M_RESET, M_MOVE };
-enum MpsFlag : uint8_t { F_CENTER_RIGHT = 1, F_POSTSELECT = 2, F_XERR = 4 };
+enum MpsKind : uint8_t { M_G1 = 0, M_G2, M_CH1, M_CH2, M_MEAS, M_RESET, M_MOVE, M_PSWAP };
+// F_PROD_LEFT: M_PSWAP whose product-state qubit sits on the left site of the pair
+enum MpsFlag : uint8_t { F_CENTER_RIGHT = 1, F_POSTSELECT = 2, F_XERR = 4, F_PROD_LEFT = 8 };
 struct MpsOp {
     uint8_t kind;
     uint8_t flags;
@@ -91,7 +92,8 @@ struct CircuitImpl {
     std::vector<uint8_t> chan_kind;
     std::vector<uint8_t> decided;  // per M instruction (text order)
     int64_t n_meas = 0, n_decided = 0, n_resets = 0, n_t = 0, n_readouts = 0;
-    int64_t n_updates = 0;
+    int64_t n_updates = 0;  // two-site updates and centre moves per shot
+    int64_t n_pswaps = 0;   // SWAPs with a product-state qubit (no decomposition)
     std::vector<PreOp> pre;
     std::vector<MpsOp> mps;
     std::mutex mu;

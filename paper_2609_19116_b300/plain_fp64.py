@@ -6,13 +6,17 @@ split, complex128 throughout -- written only so that the batched engine's throug
 compared with it.  It is not part of the sampling path and shares nothing with the CUDA library
 except the fault lists, which it takes as input.
 
-Semantics follow the engine: SWAP routing for non-adjacent gates (Sec. 3.1), the truncation rule
-(smallest kept count whose discarded tail is <= cutoff, at most chi_max), readouts from the Born
-rule with the 53-bit Philox uniforms of the random-number contract, early stop at the first
-measurement returning 1 (Sec. 4.3).
+Semantics follow the engine: SWAP routing for non-adjacent gates (Sec. 3.1) with the engine's
+routing rules (a moved qubit stays where it was moved; the mover is the unentangled qubit, else the
+one reset first, else the one whose next partner is nearer; a reset qubit walks home; a logical
+SWAP relabels; a SWAP with an unentangled qubit is an exact relabelling of bonds), the truncation
+rule (smallest kept count whose discarded tail is <= cutoff, at most chi_max), readouts from the
+Born rule with the 53-bit Philox uniforms of the random-number contract, early stop at the first
+measurement returning 1 (Sec. 4.3).  Instructions run in text order.
 """
 from __future__ import annotations
 
+import bisect
 import math
 
 import numpy as np
@@ -124,16 +128,39 @@ class PlainMPS:
         self.center = q + 1
         self.updates += 1
 
-    def gate2(self, g4, a, b, sw):
-        if abs(a - b) == 1:
-            self.two_site(g4 if a < b else sw @ g4 @ sw, min(a, b))
+    def product_swap(self, k, prod_left):
+        """SWAP of sites k, k+1 where one qubit is unentangled: A = phi (x) M, no SVD.  When the
+        relabelled bond would be wider than the other side allows (a readout leaves bonds wider
+        than the state needs) or the tensor does not show the product form, the SWAP goes
+        through the SVD instead (exact either way)."""
+        l, r = self.A[k].shape[0], self.A[k + 1].shape[2]
+        p = k if prod_left else k + 1
+        a = self.A[p]
+        rho = torch.einsum("lsr,ltr->st", a, a.conj())
+        ev = torch.linalg.eigvalsh(rho)
+        # a QR move through a site whose matrix is rank-deficient completes Q with directions
+        # outside the qubit's state, so the tensor need not show the product form: use the SVD
+        if (prod_left and r > 2 * l) or (not prod_left and l > 2 * r) or float(ev[0]) > 1e-12 * float(ev[1]):
+            self.two_site(torch.tensor([[1, 0, 0, 0], [0, 0, 1, 0], [0, 1, 0, 0], [0, 0, 0, 1]],
+                                       dtype=self.A[k].dtype, device=self.dev), k)
             return
-        lo, hi = min(a, b), max(a, b)
-        for i in range(lo, hi - 1):
-            self.two_site(sw, i)
-        self.two_site(g4 if a < b else sw @ g4 @ sw, hi - 1)
-        for i in range(hi - 2, lo - 1, -1):
-            self.two_site(sw, i)
+        s0 = int(torch.argmax(rho.diagonal().real))
+        phi = rho[:, s0] / torch.sqrt(rho[s0, s0].real * rho.diagonal().real.sum())
+        mm = torch.einsum("s,lsr->lr", phi.conj(), a)
+        if prod_left:
+            b = self.A[k + 1]
+            r = b.shape[2]
+            self.A[k] = torch.tensordot(mm, b, dims=([1], [0]))
+            self.A[k + 1] = torch.einsum("s,ab->asb", phi, torch.eye(r, dtype=a.dtype, device=self.dev))
+            if self.center in (k, k + 1):
+                self.center = k
+        else:
+            b = self.A[k]
+            l = b.shape[0]
+            self.A[k + 1] = torch.tensordot(b, mm, dims=([2], [0]))
+            self.A[k] = torch.einsum("s,ab->asb", phi, torch.eye(l, dtype=a.dtype, device=self.dev))
+            if self.center in (k, k + 1):
+                self.center = k + 1
 
     def one(self, u, q):
         self.A[q] = torch.einsum("st,ltr->lsr", u, self.A[q])
@@ -150,34 +177,115 @@ class PlainMPS:
         self.A[q] = a / torch.sqrt((a.abs() ** 2).sum())
 
 
-def run_shot(n, ops, faults, *, seed, shot, chi_max, cutoff, dev, max_updates=None):
+def plan(n, ops, return_layout=False):
+    """Routed steps in text order: ("1q", name, site) | ("ch", name, sites, aux) |
+    ("g2", name, left site, first operand on the left) | ("swap", k) | ("pswap", k, prod_left) |
+    ("read", name, site, aux).  With return_layout, also pos (logical qubit -> final site)."""
+    resets = [[] for _ in range(n)]
+    gates2 = [[] for _ in range(n)]
+    for i, (name, qs, _) in enumerate(ops):
+        if name == "R":
+            resets[qs[0]].append(i)
+        elif name in ("CX", "CZ", "SWAP"):
+            gates2[qs[0]].append(i)
+            gates2[qs[1]].append(i)
+
+    def nxt(v, i):
+        j = bisect.bisect_right(v, i)
+        return v[j] if j < len(v) else -1
+
+    pos, at, prod = list(range(n)), list(range(n)), [True] * n
+    steps = []
+
+    def swap(k):
+        x, y = at[k], at[k + 1]
+        steps.append(("pswap", k, prod[x]) if (prod[x] or prod[y]) else ("swap", k))
+        at[k], at[k + 1] = y, x
+        pos[x], pos[y] = k + 1, k
+
+    for i, (name, qs, aux) in enumerate(ops):
+        if name in ("DEP1", "DEP2", "XERR"):
+            steps.append(("ch", name, tuple(pos[q] for q in qs), aux))
+        elif name == "SWAP":
+            a, b = qs
+            pos[a], pos[b] = pos[b], pos[a]
+            at[pos[a]], at[pos[b]] = a, b
+            prod[a], prod[b] = prod[b], prod[a]
+        elif name in ("CX", "CZ"):
+            a, b = qs
+            if prod[a] != prod[b]:
+                mv = a if prod[a] else b
+            else:
+                ra, rb = nxt(resets[a], i), nxt(resets[b], i)
+                if ra != rb and (ra >= 0 or rb >= 0):
+                    mv = a if (rb < 0 or (0 <= ra < rb)) else b
+                else:
+                    def score(m_, o_):
+                        d = abs(pos[m_] - pos[o_]) - 1
+                        dest = pos[o_] - 1 if pos[m_] < pos[o_] else pos[o_] + 1
+                        j = nxt(gates2[m_], i)
+                        if j >= 0:
+                            q2 = ops[j][1]
+                            partner = q2[1] if q2[0] == m_ else q2[0]
+                            if partner != o_:
+                                d += 0.5 * max(0, abs(dest - pos[partner]) - 1)
+                        return d
+                    mv = a if score(a, b) <= score(b, a) else b
+            other = b if mv == a else a
+            while abs(pos[mv] - pos[other]) > 1:
+                swap(pos[mv] if pos[mv] < pos[other] else pos[mv] - 1)
+            steps.append(("g2", name, min(pos[a], pos[b]), pos[a] < pos[b]))
+            prod[a] = prod[b] = False
+        elif name in ("M", "R"):
+            q = qs[0]
+            steps.append(("read", name, pos[q], aux))
+            prod[q] = True
+            if name == "R":
+                while pos[q] != q:
+                    swap(pos[q] - 1 if pos[q] > q else pos[q])
+        else:
+            steps.append(("1q", name, pos[qs[0]]))
+    return (steps, pos) if return_layout else steps
+
+
+def n_svd_updates(steps):
+    return sum(1 for st in steps if st[0] in ("g2", "swap"))
+
+
+def run_shot(n, ops, faults, *, seed, shot, chi_max, cutoff, dev, max_updates=None, steps=None):
     """One shot; returns (status, updates).  faults: dict channel -> pauli code."""
     one, two, paulis = _gates(dev)
     m = PlainMPS(n, chi_max, cutoff, dev)
     sw = two["SWAP"]
-    for name, qs, aux in ops:
+    for st in (steps if steps is not None else plan(n, ops)):
         if max_updates is not None and m.updates >= max_updates:
             return "cut", m.updates
-        if name in one:
-            m.one(one[name], qs[0])
-        elif name in two:
-            m.gate2(two[name], qs[0], qs[1], sw)
-        elif name in ("DEP1", "DEP2", "XERR"):
-            code = faults.get(aux)
+        kind = st[0]
+        if kind == "1q":
+            m.one(one[st[1]], st[2])
+        elif kind == "g2":
+            g = two[st[1]]
+            m.two_site(g if st[3] else sw @ g @ sw, st[2])
+        elif kind == "swap":
+            m.two_site(sw, st[1])
+        elif kind == "pswap":
+            m.product_swap(st[1], st[2])
+        elif kind == "ch":
+            code = faults.get(st[3])
             if code:
-                if name == "DEP2":
-                    m.one(paulis[code >> 2], qs[0])
-                    m.one(paulis[code & 3], qs[1])
+                if st[1] == "DEP2":
+                    m.one(paulis[code >> 2], st[2][0])
+                    m.one(paulis[code & 3], st[2][1])
                 else:
-                    m.one(paulis[code], qs[0])
+                    m.one(paulis[code], st[2][0])
         else:
-            q = qs[0]
+            q = st[2]
             p1 = m.prob1(q)
-            o = 1 if readout_uniform(seed, aux, shot) < p1 else 0
-            if name == "M" and o == 1:
+            o = 1 if readout_uniform(seed, st[3], shot) < p1 else 0
+            if st[1] == "M" and o == 1:
                 return "rejected", m.updates
             m.project(q, o)
-            if name == "R" and o == 1:
+            if st[1] == "R" and o == 1:
                 m.one(one["X"], q)
     if str(dev).startswith("cuda"):
         torch.cuda.synchronize()

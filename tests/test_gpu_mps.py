@@ -107,19 +107,40 @@ def test_random_circuits_match_statevector(seed, prec):
 
 
 def test_truncation_invariants():
-    """chi_max below the Schmidt rank: bonds capped, discarded weight reported, F <= 1."""
+    """chi_max below the Schmidt rank: bonds capped, discarded weight reported, F <= 1.  Truncation
+    does not commute with reordering: the engine's locality schedule and routing apply the same
+    gates in another order than the oracle's text order, and both are valid truncations, so the
+    discarded weights agree only roughly (a sanity bound, not parity)."""
     q = lib_ready()
-    text = random_circuit(10, 300, seed=3, max_dist=2, noise=False, one_q=("H", "T", "S"))
+    for max_dist in (1, 2):
+        text = random_circuit(10, 300, seed=3, max_dist=max_dist, noise=False, one_q=("H", "T", "S"),
+                              two_q=("CX", "CZ"))
+        c = q.Circuit(text)
+        _, res = q.mps_sample_batch(c, dev_shots([0, 1]), p=0.0, seed=0, chi_max=4, cutoff=0.0,
+                                    precision=q.QC_C128)
+        oc = parse(text)
+        _, trunc, _ = omps.run_shot(oc, reference=True, chi_max=4)
+        assert trunc.discarded > 0
+        for r in res:
+            assert r["status"] == 0 and r["chi_peak"] <= 4
+            assert r["discarded"] > 0
+            assert r["fidelity"] <= 1 + 1e-12
+            assert abs(r["discarded"] - trunc.discarded) < 0.1 * trunc.discarded
+
+
+@pytest.mark.parametrize("prec", [1, 0])
+def test_long_range_routing_matches_statevector(prec):
+    """Gates up to 7 sites apart with frequent resets and logical SWAPs: moved qubits stay where
+    routing left them, reset qubits walk home by product SWAPs; the sampled results equal the
+    statevector's."""
+    q = lib_ready()
+    text = random_circuit(10, 220, seed=11, max_dist=7, p_reset=0.08)
     c = q.Circuit(text)
-    _, res = q.mps_sample_batch(c, dev_shots([0, 1]), p=0.0, seed=0, chi_max=4, cutoff=0.0, precision=q.QC_C128)
-    oc = parse(text)
-    _, exact, _ = omps.run_shot(oc, reference=True)
-    _, trunc, _ = omps.run_shot(oc, reference=True, chi_max=4)
-    for r in res:
-        assert r["status"] == 0 and r["chi_peak"] <= 4
-        assert r["discarded"] > 0
-        if r["degenerate_cuts"] == 0 and trunc.degenerate_cuts == 0:
-            assert abs(r["discarded"] - trunc.discarded) < 1e-9
+    assert c.info()["n_product_swaps"] > 0
+    shots = list(range(0, 40))
+    _, res = q.mps_sample_batch(c, dev_shots(shots), p=2e-2, seed=4, chi_max=64, cutoff=0.0, precision=prec)
+    ref = _oracle_results(text, shots, p=2e-2, seed=4, engine="sv")
+    _compare(res, ref, 1e-10 if prec == 1 else 1e-4, allow_flip=0 if prec == 1 else 1)
 
 
 def test_exact_weight_mode():
