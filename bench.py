@@ -257,18 +257,19 @@ def comparator_leg(q, text, circ, shot, args, time_cap_s=40.0):
     cnt, chan, code = q.qc_sample_faults(circ, shots, p=args.p, seed=args.seed, max_faults=128)
     k = int(cnt[0])
     faults = dict(zip(chan[0, :k].tolist(), code[0, :k].tolist()))
-    total = sum(2 * abs(qs[0] - qs[1]) - 1 for name, qs, _ in ops if name in ("CX", "CZ", "SWAP"))
+    steps = pf.plan(n, ops)
+    total = pf.n_svd_updates(steps)
     # warm the library (cuSOLVER handles), calibrate the update rate on a prefix, then run to the cap
     pf.run_shot(n, ops, faults, seed=args.seed, shot=shot, chi_max=args.chi_max, cutoff=args.cutoff, dev="cuda",
-                max_updates=50)
+                max_updates=50, steps=steps)
     t0 = time.perf_counter()
     st, upd = pf.run_shot(n, ops, faults, seed=args.seed, shot=shot, chi_max=args.chi_max, cutoff=args.cutoff,
-                          dev="cuda", max_updates=300)
+                          dev="cuda", max_updates=300, steps=steps)
     rate = upd / (time.perf_counter() - t0)
     cap_updates = int(rate * time_cap_s)
     t0 = time.perf_counter()
     st, upd = pf.run_shot(n, ops, faults, seed=args.seed, shot=shot, chi_max=args.chi_max, cutoff=args.cutoff,
-                          dev="cuda", max_updates=cap_updates)
+                          dev="cuda", max_updates=cap_updates, steps=steps)
     dt = time.perf_counter() - t0
     extrapolated = st == "cut"
     per_shot_s = dt * (total / max(1, upd)) if extrapolated else dt

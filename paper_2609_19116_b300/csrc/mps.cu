@@ -169,7 +169,7 @@ struct Engine {
     int chi_peak;
     int nupd;
     int64_t abort_op;
-    double flops;
+    unsigned long long flops;  // algorithmic flops of this shot (integer counts, thread 0)
     int sweeps;
 
     const int tid_;  // thread index within the engine (the warp lane in warp mode)
@@ -235,6 +235,63 @@ struct Engine {
         return (R)block_sum<NT>((double)v, S.red, tid_);
     }
 
+    // ---- one column pair of the Jacobi sweep -------------------------------------------------------
+    // Dot products over this lane's rows i = gl, gl+g, ...: alpha = |a|^2, beta = |b|^2,
+    // gamma = a^H b = gr + i gi.  Complex64 uses the paired FP32 FMA (two lanes of one 64-bit
+    // register per instruction): the real and imaginary parts accumulate separately and are added
+    // at the end.
+    __device__ __forceinline__ void pair_dots(const V* a, const V* b, int rows, int gl, int g, R& al, R& be,
+                                              R& gr, R& gi) {
+        if constexpr (sizeof(R) == 4) {
+            float2 sa = make_float2(0.f, 0.f), sb = sa, sg = sa, sh = sa;
+            for (int i = gl; i < rows; i += g) {
+                const float2 x = a[i], y = b[i];
+                sa = __ffma2_rn(x, x, sa);
+                sb = __ffma2_rn(y, y, sb);
+                sg = __ffma2_rn(x, y, sg);                            // (x.re y.re, x.im y.im)
+                sh = __ffma2_rn(x, make_float2(y.y, y.x), sh);         // (x.re y.im, x.im y.re)
+            }
+            al = sa.x + sa.y;
+            be = sb.x + sb.y;
+            gr = sg.x + sg.y;
+            gi = sh.x - sh.y;
+        } else {
+            for (int i = gl; i < rows; i += g) {
+                const V x = a[i], y = b[i];
+                al = fma(x.x, x.x, fma(x.y, x.y, al));
+                be = fma(y.x, y.x, fma(y.y, y.y, be));
+                gr = fma(x.x, y.x, fma(x.y, y.y, gr));
+                gi = fma(x.x, y.y, fma(-x.y, y.x, gi));
+            }
+        }
+    }
+
+    // The rotation of one pair: a <- c a - w b,  b <- conj(w) a + c b,  w = s e^{-i phi} = (wr, wi).
+    __device__ __forceinline__ void pair_rotate(V* a, V* b, int rows, int gl, int g, R c, R wr, R wi) {
+        if constexpr (sizeof(R) == 4) {
+            const float2 cc = make_float2(c, c), nw = make_float2(-wr, -wr), ws = make_float2(wi, -wi);
+            const float2 wp = make_float2(wr, wr);
+            for (int i = gl; i < rows; i += g) {
+                const float2 x = a[i], y = b[i];
+                float2 t = __fmul2_rn(nw, y);                          // -w y
+                t = __ffma2_rn(ws, make_float2(y.y, y.x), t);
+                float2 u = __fmul2_rn(cc, y);                          // conj(w) x + c y
+                u = __ffma2_rn(wp, x, u);
+                u = __ffma2_rn(ws, make_float2(x.y, x.x), u);
+                a[i] = __ffma2_rn(cc, x, t);
+                b[i] = u;
+            }
+        } else {
+            for (int i = gl; i < rows; i += g) {
+                const V x = a[i], y = b[i];
+                const R wyx = wr * y.x - wi * y.y, wyy = wr * y.y + wi * y.x;  // w y
+                const R vxx = wr * x.x + wi * x.y, vxy = wr * x.y - wi * x.x;  // conj(w) x
+                a[i] = cmk<V>(c * x.x - wyx, c * x.y - wyy);
+                b[i] = cmk<V>(vxx + c * y.x, vxy + c * y.y);
+            }
+        }
+    }
+
     // ---- one-sided Jacobi on the columns of X (rows x cols, leading dimension ld) ---------------
     // Round-robin ordering: n-1 rounds of n/2 disjoint column pairs.  The pairs of a round are
     // spread over the warps, and within a warp over lane groups of g lanes (g = 32 / pairs per warp,
@@ -262,19 +319,16 @@ struct Engine {
                     const int pr = base + grp;
                     const bool act = pr < half;
                     const int sa = act ? pr : 0, sb = cols - 1 - sa;
-                    const int ca = sa == 0 ? 0 : 1 + (sa - 1 + k) % cm1;
-                    const int cb = 1 + (sb - 1 + k) % cm1;
+                    // round-robin position -> column: 1 + (s - 1 + k) mod (cols - 1), both terms < cols - 1
+                    int ia = sa - 1 + k, ib = sb - 1 + k;
+                    ia -= ia >= cm1 ? cm1 : 0;
+                    ib -= ib >= cm1 ? cm1 : 0;
+                    const int ca = sa == 0 ? 0 : 1 + ia;
+                    const int cb = 1 + ib;
                     V* a = X + (size_t)ca * ld;
                     V* b = X + (size_t)cb * ld;
                     R al = 0, be = 0, gr = 0, gi = 0;
-                    if (act)
-                        for (int i = gl; i < rows; i += g) {
-                            const V x = a[i], y = b[i];
-                            al = fma(x.x, x.x, fma(x.y, x.y, al));
-                            be = fma(y.x, y.x, fma(y.y, y.y, be));
-                            gr = fma(x.x, y.x, fma(x.y, y.y, gr));
-                            gi = fma(x.x, y.y, fma(-x.y, y.x, gi));
-                        }
+                    if (act) pair_dots(a, b, rows, gl, g, al, be, gr, gi);
                     for (int o = g >> 1; o > 0; o >>= 1) {
                         al += __shfl_xor_sync(0xFFFFFFFFu, al, o);
                         be += __shfl_xor_sync(0xFFFFFFFFu, be, o);
@@ -288,14 +342,7 @@ struct Engine {
                         const R zeta = (be - al) * (R)0.5 * rg;
                         const R t = fdiv(zeta >= 0 ? (R)1 : (R)-1, fabs(zeta) + sqrt((R)1 + zeta * zeta));
                         const R c = rs_sqrt((R)1 + t * t), sn = c * t;
-                        const R er = gr * rg, ei = gi * rg;
-                        for (int i = gl; i < rows; i += g) {
-                            const V x = a[i], y = b[i];
-                            const R emx = er * y.x + ei * y.y, emy = er * y.y - ei * y.x;  // e^{-i phi} y
-                            const R epx = er * x.x - ei * x.y, epy = er * x.y + ei * x.x;  // e^{+i phi} x
-                            a[i] = cmk<V>(c * x.x - sn * emx, c * x.y - sn * emy);
-                            b[i] = cmk<V>(sn * epx + c * y.x, sn * epy + c * y.y);
-                        }
+                        pair_rotate(a, b, rows, gl, g, c, sn * gr * rg, -sn * gi * rg);
                     }
                 }
                 bsync<NT>();
@@ -322,8 +369,11 @@ struct Engine {
             for (int k = 0; k < nbp - 1; ++k) {
                 for (int pr = 0; pr < nbp / 2; ++pr) {
                     const int sa = pr, sb = nbp - 1 - pr;
-                    const int bi = sa == 0 ? 0 : 1 + (sa - 1 + k) % (nbp - 1);
-                    const int bj = 1 + (sb - 1 + k) % (nbp - 1);
+                    int ia = sa - 1 + k, ib = sb - 1 + k;
+                    ia -= ia >= nbp - 1 ? nbp - 1 : 0;
+                    ib -= ib >= nbp - 1 ? nbp - 1 : 0;
+                    const int bi = sa == 0 ? 0 : 1 + ia;
+                    const int bj = 1 + ib;
                     const int i0 = bi * bw, i1 = min(cols, i0 + bw);
                     const int j0 = bj * bw, j1 = min(cols, j0 + bw);
                     const int ni = bi < nb ? i1 - i0 : 0, nj = bj < nb ? j1 - j0 : 0;
@@ -387,36 +437,59 @@ struct Engine {
             perm[rk] = j;
         }
         bsync<NT>();
-        // truncation rule, FP64: smallest r >= 1 with discarded tail <= cutoff * total, r <= chi_max
-        if (tid_ == 0) {
-            double tot = 0;
-            int nz = 0;
-            for (int k = 0; k < cols; ++k) {
-                tot += (double)sig2[k];
-                nz += sig2[k] > floor2;
+        // truncation rule, FP64: smallest r >= 1 with discarded tail <= cutoff * total, r <= chi_max.
+        // The first warp works on the sorted values in contiguous chunks, one per lane: chunk sums,
+        // a suffix scan over the lanes, then every position k >= 1 whose tail sum_{k' >= k} s_k'^2
+        // exceeds the threshold is counted (the tail shrinks with k, so those positions are
+        // 1 .. r-1).
+        if (tid_ < 32) {
+            const unsigned full = 0xFFFFFFFFu;
+            const int lane = tid_;
+            const int c = (cols + 31) >> 5;
+            const int k0 = min(cols, lane * c), k1 = min(cols, k0 + c);
+            double loc = 0;
+            int nzl = 0;
+            for (int k = k0; k < k1; ++k) {
+                const R v = sig2[perm[k]];
+                loc += (double)v;
+                nzl += v > floor2;
             }
+            double incl = loc;  // sum of this lane's chunk and every later one
+            for (int o = 1; o < 32; o <<= 1) {
+                const double t = __shfl_down_sync(full, incl, o);
+                if (lane + o < 32) incl += t;
+            }
+            const double tot = __shfl_sync(full, incl, 0);
+            double after = __shfl_down_sync(full, incl, 1);
+            if (lane == 31) after = 0;
+            const int nz = __reduce_add_sync(full, nzl);
             const double thr = P.cutoff * tot;
-            int r = cols;
-            double tail = 0;
-            while (r > 1 && tail + (double)sig2[perm[r - 1]] <= thr) {
-                tail += (double)sig2[perm[r - 1]];
-                --r;
+            int cnt = 0;
+            double tail = after;
+            for (int k = k1 - 1; k >= k0; --k) {
+                tail += (double)sig2[perm[k]];
+                cnt += (k >= 1 && tail > thr);
             }
-            while (r > P.chi_trunc || (r > 1 && r > nz)) {
-                tail += (double)sig2[perm[r - 1]];
-                --r;
+            int r = 1 + __reduce_add_sync(full, cnt);
+            r = min(r, P.chi_trunc);
+            r = min(r, max(nz, 1));
+            double kl = 0, tl = 0;
+            for (int k = k0; k < k1; ++k) {
+                const double v = (double)sig2[perm[k]];
+                if (k < r) kl += v; else tl += v;
             }
-            double kept = 0;
-            for (int k = 0; k < r; ++k) kept += (double)sig2[perm[k]];
-            int dg = 0;
-            if (r < cols) {
-                const double sa = sqrt((double)sig2[perm[r - 1]]), sb = sqrt((double)sig2[perm[r]]);
-                dg = (sb > 0 && sa / sb - 1.0 < 1e-8);
+            const double kept = warp_sum<double>(kl), dropped = warp_sum<double>(tl);
+            if (lane == 0) {
+                int dg = 0;
+                if (r < cols) {  // s_{r-1} / s_r - 1 < 1e-8, compared on the squares
+                    const double a2 = (double)sig2[perm[r - 1]], b2 = (double)sig2[perm[r]];
+                    dg = b2 > 0 && a2 < b2 * (1.0 + 2e-8 + 1e-16);
+                }
+                S.red[40] = tot > 0 ? dropped / tot : 0.0;
+                S.red[41] = kept > 0 ? 1.0 / sqrt(kept) : 0.0;
+                S.red[42] = (double)r;
+                S.red[43] = (double)dg;
             }
-            S.red[40] = tot > 0 ? tail / tot : 0.0;
-            S.red[41] = kept > 0 ? 1.0 / sqrt(kept) : 0.0;
-            S.red[42] = (double)r;
-            S.red[43] = (double)dg;
         }
         bsync<NT>();
         const int r = (int)S.red[42];
@@ -532,7 +605,7 @@ struct Engine {
                 T[e] = right ? v : cmk<V>(v.x, -v.y);
             }
         }
-        const double frod = block_sum<NT>((double)fro, S.red, tid_);
+        const double frod = (double)sum_r(fro);  // sets the numerical floor only: working precision
         const R eps = sizeof(R) == 4 ? (R)FLT_EPSILON : (R)DBL_EPSILON;
         const R fl = (R)4 * eps * sqrt((R)rows);
         const R floor2 = fl * fl * (R)frod;
@@ -596,10 +669,10 @@ struct Engine {
         bsync<NT>();
         chi_peak = max(chi_peak, r);
         ++nupd;
-        if (tid_ == 0) {  // accounting in FP64 on one thread: the FP64 pipe is narrow on this part
-            const double M = (double)max(m, n), Nn = (double)min(m, n);
-            flops += 8.0 * m * cm * n + 128.0 * cl * cr + 4.0 * (4.0 * M * M * Nn + 22.0 * Nn * Nn * Nn) +
-                     8.0 * r * m * n;
+        if (tid_ == 0) {  // integer accounting: the FP64 pipe is narrow on this part
+            const unsigned long long M = max(m, n), Nn = min(m, n);
+            flops += 8ull * m * cm * n + 128ull * cl * cr + 4ull * (4ull * M * M * Nn + 22ull * Nn * Nn * Nn) +
+                     8ull * r * m * n;
         }
     }
 
@@ -709,7 +782,7 @@ struct Engine {
         for (int e = tid_; e < cm * cm; e += NT) Rm[e] = cmk<V>(0, 0);
         const V* Bo = right ? (fast ? O : B) : B;
         const V* Ao = right ? A : (fast ? O : A);
-        const double frod = block_sum<NT>((double)fro, S.red, tid_);
+        const double frod = (double)sum_r(fro);  // sets the numerical floor only: working precision
         const R eps = sizeof(R) == 4 ? (R)FLT_EPSILON : (R)DBL_EPSILON;
         const R fl = (R)4 * eps * sqrt((R)rows);
         const R floor2 = fl * fl * (R)frod;
@@ -721,7 +794,7 @@ struct Engine {
             status = QC_ENOCONV;
             return;
         }
-        if (frod > 0) disc += dropped / frod;
+        if (dropped > 0 && frod > 0) disc += dropped / frod;
         if (right) {
             // A[q] = Q (cl, 2, r);  A[q+1] = R B (r, 2, cr), R upper triangular in column order
             for (int e = tid_; e < r * n; e += NT) {
@@ -759,8 +832,8 @@ struct Engine {
         bsync<NT>();
         ++nupd;
         if (tid_ == 0) {  // Householder QR count of the rows x cm factor, plus the product with R
-            const double M = (double)max(rows, cm), K = (double)min(rows, cm);
-            flops += 8.0 * (M * K * K - K * K * K / 3.0) + 8.0 * r * cm * (right ? n : m);
+            const unsigned long long M = max(rows, cm), K = min(rows, cm);
+            flops += (24ull * M * K * K - 8ull * K * K * K) / 3ull + 8ull * r * cm * (right ? n : m);
         }
     }
 
@@ -844,7 +917,7 @@ struct Engine {
                 }
             }
             for (int e = tid_; e < cols * cols; e += NT) Rm[e] = cmk<V>(0, 0);
-            const double frod = block_sum<NT>((double)fro, S.red, tid_);
+            const double frod = (double)sum_r(fro);  // sets the numerical floor only: working precision
             const R eps = sizeof(R) == 4 ? (R)FLT_EPSILON : (R)DBL_EPSILON;
             const R fl = (R)4 * eps * sqrt((R)rows);
             const R floor2 = fl * fl * (R)frod;
@@ -859,7 +932,7 @@ struct Engine {
                 status = QC_ECAPACITY;
                 return;
             }
-            if (frod > 0) disc += dropped / frod;
+            if (dropped > 0 && frod > 0) disc += dropped / frod;
             nb = k;
             if (prod_left) {
                 // A[q](l, t, kk) = conj R[kk, (l, t)];  A[q+1](kk, s, r) = [s = 0] conj Q[r, kk]
@@ -886,8 +959,8 @@ struct Engine {
                 for (int e = tid_; e < k * cols; e += NT) B[e] = Rm[e];
             }
             if (tid_ == 0) {
-                const double M = (double)max(rows, cols), K = (double)min(rows, cols);
-                flops += 8.0 * (M * K * K - K * K * K / 3.0);
+                const unsigned long long M = max(rows, cols), K = min(rows, cols);
+                flops += (24ull * M * K * K - 8ull * K * K * K) / 3ull;
             }
         }
         bsync<NT>();
@@ -898,7 +971,7 @@ struct Engine {
                 S.pend[q * 4 + k] = S.pend[(q + 1) * 4 + k];
                 S.pend[(q + 1) * 4 + k] = t;
             }
-            flops += 16.0 * cl * cm * cr;
+            flops += 16ull * cl * cm * cr;
         }
         bsync<NT>();
         chi_peak = max(chi_peak, nb);
@@ -1189,7 +1262,7 @@ struct Engine {
                     res.discarded = disc;
                     res.degenerate_cuts = degen;
                     res.n_updates = nupd;
-                    res.alg_flops = flops;
+                    res.alg_flops = (double)flops;
                     res.sweeps = sweeps;
                     P.per_shot[task] = res;
                 }

@@ -143,6 +143,7 @@ class PlainMPS:
         if (prod_left and r > 2 * l) or (not prod_left and l > 2 * r) or float(ev[0]) > 1e-12 * float(ev[1]):
             self.two_site(torch.tensor([[1, 0, 0, 0], [0, 0, 1, 0], [0, 1, 0, 0], [0, 0, 0, 1]],
                                        dtype=self.A[k].dtype, device=self.dev), k)
+            self.updates -= 1  # counted as the product SWAP it stands for
             return
         s0 = int(torch.argmax(rho.diagonal().real))
         phi = rho[:, s0] / torch.sqrt(rho[s0, s0].real * rho.diagonal().real.sum())
