@@ -504,7 +504,9 @@ def main():
         "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                      "frac": achieved / alu_peak if alu_peak else None, "traffic": None,
                      "kernel": "engine_kernel<float,32> (one warp per shot)",
-                     "peak_note": "FP32 FMA issue rate 148 SM x 128 lanes x 2 x sm_max_mhz (MEASURED_PEAKS sm_max_mhz)",
+                     "peak_note": "FP32 FMA issue rate 148 SM x 128 lanes x 2 x %.0f MHz (%s)" % (
+                         smax, "sm_max_mhz of MEASURED_PEAKS.json" if "sm_max_mhz" in peaks
+                         else "fallback: the B300's maximum SM clock, MEASURED_PEAKS.json absent"),
                      "alg_flops_per_shot": flops_last / max(1, last["n"]), "engine_ms": eng_ms},
         "clocks": clocks,
         "e2e": {"value": e2e_val, "unit": "shots/s", "h2d_bytes_per_step": h2d // e2e_steps,

@@ -516,7 +516,10 @@ struct Engine {
         bsync<NT>();  // pending gates written by thread 0, dims of the previous update
         const int cl = S.dims[q], cm = S.dims[q + 1], cr = S.dims[q + 2];
         const int m = 2 * cl, n = 2 * cr;
-        const int rows = right ? m : n, cols = right ? n : m;
+        // the Jacobi orthogonalises the columns of theta' (xt) or of theta'^H, whichever has fewer
+        // (cost ~ rows x cols^2); a square theta' follows the centre's direction
+        const bool xt = n < m || (n == m && right);
+        const int rows = xt ? m : n, cols = xt ? n : m;
         const int ld = rows + 1;
         const uint64_t ab = (uint64_t)m * cm + (uint64_t)cm * n;
         const uint64_t treg = max((uint64_t)m * n, ab);
@@ -593,7 +596,7 @@ struct Engine {
                 const int i = l * 2 + (st >> 1), j = (st & 1) * cr + r;
                 fro = fma(v.x, v.x, fma(v.y, v.y, fro));
                 if (!fast) T[(size_t)i * n + j] = v;
-                if (right) X[(size_t)j * ld + i] = v;
+                if (xt) X[(size_t)j * ld + i] = v;
                 else X[(size_t)i * ld + j] = cmk<V>(v.x, -v.y);
             }
         }
@@ -601,8 +604,8 @@ struct Engine {
             bsync<NT>();
             for (int e = tid_; e < m * n; e += NT) {
                 const int i = e / n, j = e - i * n;
-                const V v = right ? X[(size_t)j * ld + i] : X[(size_t)i * ld + j];
-                T[e] = right ? v : cmk<V>(v.x, -v.y);
+                const V v = xt ? X[(size_t)j * ld + i] : X[(size_t)i * ld + j];
+                T[e] = xt ? v : cmk<V>(v.x, -v.y);
             }
         }
         const double frod = (double)sum_r(fro);  // sets the numerical floor only: working precision
@@ -635,8 +638,8 @@ struct Engine {
         bsync<NT>();
         V* As = site(q);
         V* Bs = site(q + 1);
-        if (right) {
-            // A[q] = U (cl, 2, r);  A[q+1] = scale * U^H theta' (r, 2, cr)
+        if (xt && right) {
+            // X = theta' = U S V^H:  A[q] = U (cl, 2, r);  A[q+1] = scale * U^H theta' (r, 2, cr)
             for (int e = tid_; e < m * r; e += NT) {
                 const int i = e / r, k = e - i * r;
                 As[e] = X[(size_t)perm[k] * ld + i];
@@ -648,8 +651,8 @@ struct Engine {
                 for (int i = 0; i < m; ++i) acc = cfmac(u[i], T[(size_t)i * n + j], acc);
                 Bs[e] = cmk<V>(acc.x * scale, acc.y * scale);
             }
-        } else {
-            // A[q+1] = U'^H (r, 2, cr);  A[q] = scale * theta' U' (cl, 2, r)
+        } else if (!xt && !right) {
+            // X = theta'^H = U' S V'^H:  A[q+1] = U'^H (r, 2, cr);  A[q] = scale * theta' U' (cl, 2, r)
             for (int e = tid_; e < r * n; e += NT) {
                 const int k = e / n, j = e - k * n;
                 const V u = X[(size_t)perm[k] * ld + j];
@@ -661,6 +664,42 @@ struct Engine {
                 V acc = cmk<V>(0, 0);
                 for (int j = 0; j < n; ++j) acc = cfma(T[(size_t)i * n + j], u[j], acc);
                 As[e] = cmk<V>(acc.x * scale, acc.y * scale);
+            }
+        } else if (xt) {
+            // X = theta' = U S V^H, centre to the left:  A[q] = scale * U S (cl, 2, r);
+            // A[q+1] = V^H = S^-1 U^H theta' (r, 2, cr)
+            for (int e = tid_; e < m * r; e += NT) {
+                const int i = e / r, k = e - i * r;
+                const R f = scale * sqrt(sig2[perm[k]]);
+                const V u = X[(size_t)perm[k] * ld + i];
+                As[e] = cmk<V>(u.x * f, u.y * f);
+            }
+            for (int e = tid_; e < r * n; e += NT) {
+                const int k = e / n, j = e - k * n;
+                const V* u = X + (size_t)perm[k] * ld;
+                V acc = cmk<V>(0, 0);
+                for (int i = 0; i < m; ++i) acc = cfmac(u[i], T[(size_t)i * n + j], acc);
+                const R sgk = sig2[perm[k]];
+                const R inv = sgk > (R)0 ? (R)1 / sqrt(sgk) : (R)0;
+                Bs[e] = cmk<V>(acc.x * inv, acc.y * inv);
+            }
+        } else {
+            // X = theta'^H = U' S V'^H (theta' = V' S U'^H), centre to the right:
+            // A[q] = V' = theta' U' S^-1 (cl, 2, r);  A[q+1] = scale * S U'^H (r, 2, cr)
+            for (int e = tid_; e < r * n; e += NT) {
+                const int k = e / n, j = e - k * n;
+                const R f = scale * sqrt(sig2[perm[k]]);
+                const V u = X[(size_t)perm[k] * ld + j];
+                Bs[e] = cmk<V>(u.x * f, -u.y * f);
+            }
+            for (int e = tid_; e < m * r; e += NT) {
+                const int i = e / r, k = e - i * r;
+                const V* u = X + (size_t)perm[k] * ld;
+                V acc = cmk<V>(0, 0);
+                for (int j = 0; j < n; ++j) acc = cfma(T[(size_t)i * n + j], u[j], acc);
+                const R sgk = sig2[perm[k]];
+                const R inv = sgk > (R)0 ? (R)1 / sqrt(sgk) : (R)0;
+                As[e] = cmk<V>(acc.x * inv, acc.y * inv);
             }
         }
         bsync<NT>();
