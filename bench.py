@@ -111,6 +111,23 @@ def measured_peaks():
         return {}
 
 
+# DRAM bytes (read + write) of one engine launch of the benchmark step, from the ncu launch list
+# (profiles/launches_d5_49q_60l_bench.md), valid only for the engine source it was taken on
+ENGINE_TRAFFIC = {"mps_cu_sha256": "9d8947e81a1483ea5621ee9ea878f14297c89d3ba02bb8346dc6ed414e4e7bb2",
+                  "bytes_per_launch": 34.16e9 + 100.32e9}
+
+
+def engine_traffic():
+    """The recorded per-launch traffic when the engine source is unchanged since the capture."""
+    import hashlib
+    path = os.path.join(HERE, "paper_2609_19116_b300", "csrc", "mps.cu")
+    try:
+        digest = hashlib.sha256(open(path, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    return ENGINE_TRAFFIC["bytes_per_launch"] if digest == ENGINE_TRAFFIC["mps_cu_sha256"] else None
+
+
 def fp32_alu_peak_tflops(sm_max_mhz):
     """FP32 FMA issue peak: 148 SMs x 128 FP32 lanes x 2 flops x SM clock."""
     return 148 * 128 * 2 * sm_max_mhz * 1e6 / 1e12
@@ -502,7 +519,9 @@ def main():
                    "l2": "each step reads fresh site-tensor slots and a new shot range; working set > L2"},
         "gpu_launches": args.steps * 5,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-                     "frac": achieved / alu_peak if alu_peak else None, "traffic": None,
+                     "frac": achieved / alu_peak if alu_peak else None, "traffic": engine_traffic(),
+                     "traffic_note": "DRAM read+write bytes per engine launch from one ncu capture of this "
+                                     "engine source (null when the source changed since)",
                      "kernel": "engine_kernel<float,32> (one warp per shot)",
                      "peak_note": "FP32 FMA issue rate 148 SM x 128 lanes x 2 x %.0f MHz (%s)" % (
                          smax, "sm_max_mhz of MEASURED_PEAKS.json" if "sm_max_mhz" in peaks
