@@ -733,14 +733,35 @@ struct Engine {
             for (int pass = 0; pass < 4 && k > 0; ++pass) {
                 for (int i = tid_; i < k; i += NT) {  // h_i = <q_i, x>
                     const V* qi = X + (size_t)perm[i] * ld;
-                    V h0 = cmk<V>(0, 0), h1 = cmk<V>(0, 0);
-                    int t = 0;
-                    for (; t + 1 < rows; t += 2) {
-                        h0 = cfmac(qi[t], x[t], h0);
-                        h1 = cfmac(qi[t + 1], x[t + 1], h1);
+                    V h;
+                    if constexpr (sizeof(R) == 4) {  // paired FP32 FMAs, as in the Jacobi
+                        float2 s1 = make_float2(0.f, 0.f), s2 = s1, s3 = s1, s4 = s1;
+                        int t = 0;
+                        for (; t + 1 < rows; t += 2) {
+                            const float2 u0 = qi[t], x0 = x[t], u1 = qi[t + 1], x1 = x[t + 1];
+                            s1 = __ffma2_rn(u0, x0, s1);                          // (q.re x.re, q.im x.im)
+                            s2 = __ffma2_rn(u0, make_float2(x0.y, x0.x), s2);     // (q.re x.im, q.im x.re)
+                            s3 = __ffma2_rn(u1, x1, s3);
+                            s4 = __ffma2_rn(u1, make_float2(x1.y, x1.x), s4);
+                        }
+                        if (t < rows) {
+                            const float2 u0 = qi[t], x0 = x[t];
+                            s1 = __ffma2_rn(u0, x0, s1);
+                            s2 = __ffma2_rn(u0, make_float2(x0.y, x0.x), s2);
+                        }
+                        s1 = __fadd2_rn(s1, s3);
+                        s2 = __fadd2_rn(s2, s4);
+                        h = cmk<V>(s1.x + s1.y, s2.x - s2.y);
+                    } else {
+                        V h0 = cmk<V>(0, 0), h1 = cmk<V>(0, 0);
+                        int t = 0;
+                        for (; t + 1 < rows; t += 2) {
+                            h0 = cfmac(qi[t], x[t], h0);
+                            h1 = cfmac(qi[t + 1], x[t + 1], h1);
+                        }
+                        if (t < rows) h0 = cfmac(qi[t], x[t], h0);
+                        h = cmk<V>(h0.x + h1.x, h0.y + h1.y);
                     }
-                    if (t < rows) h0 = cfmac(qi[t], x[t], h0);
-                    const V h = cmk<V>(h0.x + h1.x, h0.y + h1.y);
                     hb[i] = h;
                     V& rr = Rm[(size_t)i * cols + j];
                     rr = cmk<V>(rr.x + h.x, rr.y + h.y);
