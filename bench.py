@@ -113,8 +113,8 @@ def measured_peaks():
 
 # DRAM bytes (read + write) of one engine launch of the benchmark step, from the ncu launch list
 # (profiles/launches_d5_49q_60l_bench.md), valid only for the engine source it was taken on
-ENGINE_TRAFFIC = {"mps_cu_sha256": "9d8947e81a1483ea5621ee9ea878f14297c89d3ba02bb8346dc6ed414e4e7bb2",
-                  "bytes_per_launch": 34.16e9 + 100.32e9}
+ENGINE_TRAFFIC = {"mps_cu_sha256": "92414f5c6b90d87d899aca98bd82baae54799f1d7dcf991b3ccfed544e1de48e",
+                  "bytes_per_launch": 34.27e9 + 100.70e9}
 
 
 def engine_traffic():
