@@ -580,13 +580,29 @@ struct Engine {
             for (int u = 0; u < 4; ++u) th[u] = cmk<V>(0, 0);
             const V* a0 = A + (l * 2) * cm;
             const V* a1 = a0 + cm;
-            for (int k = 0; k < cm; ++k) {
-                const V x0 = a0[k], x1 = a1[k];
-                const V y0 = B[(size_t)k * n + r], y1 = B[(size_t)k * n + cr + r];
-                th[0] = cfma(x0, y0, th[0]);
-                th[1] = cfma(x0, y1, th[1]);
-                th[2] = cfma(x1, y0, th[2]);
-                th[3] = cfma(x1, y1, th[3]);
+            if constexpr (sizeof(R) == 4) {  // complex MACs as two paired FP32 FMAs each
+                float2 t0 = make_float2(0.f, 0.f), t1 = t0, t2 = t0, t3 = t0;
+                for (int k = 0; k < cm; ++k) {
+                    const float2 x0 = a0[k], x1 = a1[k];
+                    const float2 y0 = B[(size_t)k * n + r], y1 = B[(size_t)k * n + cr + r];
+                    const float2 x0r = make_float2(x0.x, x0.x), x0i = make_float2(-x0.y, x0.y);
+                    const float2 x1r = make_float2(x1.x, x1.x), x1i = make_float2(-x1.y, x1.y);
+                    const float2 y0s = make_float2(y0.y, y0.x), y1s = make_float2(y1.y, y1.x);
+                    t0 = __ffma2_rn(x0i, y0s, __ffma2_rn(x0r, y0, t0));
+                    t1 = __ffma2_rn(x0i, y1s, __ffma2_rn(x0r, y1, t1));
+                    t2 = __ffma2_rn(x1i, y0s, __ffma2_rn(x1r, y0, t2));
+                    t3 = __ffma2_rn(x1i, y1s, __ffma2_rn(x1r, y1, t3));
+                }
+                th[0] = t0; th[1] = t1; th[2] = t2; th[3] = t3;
+            } else {
+                for (int k = 0; k < cm; ++k) {
+                    const V x0 = a0[k], x1 = a1[k];
+                    const V y0 = B[(size_t)k * n + r], y1 = B[(size_t)k * n + cr + r];
+                    th[0] = cfma(x0, y0, th[0]);
+                    th[1] = cfma(x0, y1, th[1]);
+                    th[2] = cfma(x1, y0, th[2]);
+                    th[3] = cfma(x1, y1, th[3]);
+                }
             }
 #pragma unroll
             for (int st = 0; st < 4; ++st) {
