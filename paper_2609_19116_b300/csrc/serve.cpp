@@ -1,8 +1,8 @@
 // Serving loop: sampling jobs for different circuits and noise rates arrive while others run.
 //
 // A job is pre-screened as a whole (Sec. 4.2), then its surviving shots are cut into chunks.
-// Worker threads, one per CUDA stream, take the next chunk of any admitted job, so chunks of
-// different jobs run concurrently on the device; inside a chunk the persistent engine retires
+// Worker threads, one per CUDA stream, take the next chunk of the admitted job with the least
+// remaining work, so chunks of different jobs run concurrently on the device; inside a chunk the persistent engine retires
 // rejected shots early and back-fills their slots (Sec. 4.3).  A chunk is launched only when its
 // in-flight footprint (slots x per-shot bytes) fits the HBM budget next to the chunks already
 // running; finished chunks release their share.  Latency is measured from submission to the end
@@ -69,8 +69,15 @@ struct Server {
         }
     }
 
-    // Pick work under the lock: a job to pre-screen, or a chunk that fits the budget.
+    // Pick work under the lock: a job to pre-screen (admission order; it is cheap and tells the
+    // job's size), else a chunk of the admitted job with the least remaining work that fits the
+    // budget (shortest remaining work first: small jobs do not wait behind large ones).  Remaining
+    // work = survivors not yet handed out x the circuit's site operations per shot.
     bool pick(Job*& job, bool& pre, uint64_t& first, uint64_t& count, uint64_t& bytes) {
+        const uint64_t free_b = cfg.hbm_budget_bytes > inflight_bytes ? cfg.hbm_budget_bytes - inflight_bytes : 0;
+        Job* best = nullptr;
+        double best_work = 0;
+        uint64_t best_slots = 0;
         for (Job* j : order) {
             if (j->state != QC_PENDING || j->cancelled) continue;
             if (!j->prescreened) {
@@ -81,23 +88,29 @@ struct Server {
             }
             if (j->next >= j->survivors) continue;
             const uint64_t avail = j->survivors - j->next;
-            uint64_t n = std::min<uint64_t>(avail, CHUNK_SHOTS);
+            const uint64_t n = std::min<uint64_t>(avail, CHUNK_SHOTS);
             uint64_t slots = std::min<uint64_t>(n, (uint64_t)max_slots);
-            const uint64_t free_b = cfg.hbm_budget_bytes > inflight_bytes ? cfg.hbm_budget_bytes - inflight_bytes : 0;
             const uint64_t fit = j->footprint ? free_b / j->footprint : slots;
             if (fit == 0) continue;  // wait until memory frees up
-            slots = std::min(slots, fit);
-            job = j; pre = false;
-            first = j->next;
-            count = n;
-            bytes = slots * j->footprint;
-            j->next += n;
-            j->inflight += 1;
-            inflight_bytes += bytes;
-            if (j->start_ms < 0) j->start_ms = now_ms();
-            return true;
+            const double work = (double)avail * (double)std::max<int64_t>(1, j->circ->n_updates);
+            if (!best || work < best_work) {
+                best = j;
+                best_work = work;
+                best_slots = std::min(slots, fit);
+            }
         }
-        return false;
+        if (!best) return false;
+        Job* j = best;
+        const uint64_t n = std::min<uint64_t>(j->survivors - j->next, CHUNK_SHOTS);
+        job = j; pre = false;
+        first = j->next;
+        count = n;
+        bytes = best_slots * j->footprint;
+        j->next += n;
+        j->inflight += 1;
+        inflight_bytes += bytes;
+        if (j->start_ms < 0) j->start_ms = now_ms();
+        return true;
     }
 
     void worker() {
