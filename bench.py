@@ -112,7 +112,7 @@ def measured_peaks():
 
 
 # DRAM bytes (read + write) of one engine launch of the benchmark step, from the ncu launch list
-# (profiles/launches_d5_49q_60l_bench.md), valid only for the engine source it was taken on
+# summary under profiles/, valid only for the engine source it was taken on
 ENGINE_TRAFFIC = {"mps_cu_sha256": "a317903e6241f6ac13bb55cdba84dd3c01820400f479570f2f97f3248279e88a",
                   "bytes_per_launch": 34.48e9 + 101.59e9}
 

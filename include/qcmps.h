@@ -127,10 +127,10 @@ qc_status pauli_prescreen(const qc_circuit* circuit, qc_noise noise, uint64_t sh
                           uint64_t nshots, uint64_t* kept_mask_dev, qc_survivors* survivors,
                           uint64_t* hist_drawn, uint64_t* hist_kept, int32_t w_max, void* stream);
 
-/* The same pre-screen for callers that cannot allocate device memory: code inside an allocation-
- * free region (a stream capture they do not own, a process whose device memory is a fixed pool
- * owned by someone else, an embedding runtime that forbids cudaMalloc).  The paper has no
- * counterpart; it is a deployment convenience.  This entry point calls no cudaMalloc, cudaFree or
+/* The same pre-screen for callers that cannot allocate device memory: a process whose device
+ * memory is a fixed pool owned by someone else, or an embedding runtime that forbids cudaMalloc.
+ * (It is not for use inside a stream capture: it copies results to host memory and synchronises
+ * the stream.)  The paper has no counterpart; it is a deployment convenience.  This entry point calls no cudaMalloc, cudaFree or
  * other allocating routine: its scratch (the staged frame program, the per-weight histograms and
  * the compaction offsets) lives in one file-scope device array of about 1.1 MB that every GPU
  * loading the library holds until the process exits.
@@ -181,6 +181,9 @@ typedef struct {
                                 8(2chi_l)chi_m(2chi_r), gate 128 chi_l chi_r, split by the R-SVD count
                                 4(4 M^2 N + 22 N^3) (M >= N the sides of theta) plus the projection
                                 8 r M N */
+    int32_t gmem_updates;    /* two-site updates whose Jacobi matrix did not fit the engine's shared
+                                memory and was rotated in global memory (blocked Jacobi) */
+    int32_t reserved;
 } qc_shot_result;
 
 /* Simulate the given shots (typically pre-screen survivors) as MPS: single-site gates in place;
@@ -200,9 +203,50 @@ qc_status mps_sample_batch(const qc_circuit* circuit, qc_noise noise, const uint
                            uint64_t nshots, qc_mps_params params, qc_counts* per_w,
                            int32_t w_max, qc_shot_result* per_shot_dev, void* stream);
 
+/* Verification hooks of mps_sample_batch (the paper has no counterpart; they exist so that tests can
+ * compare intermediate quantities with a reference simulator and exercise the bounded limits).
+ *   readout_p1_dev  optional device array of nshots x readout_k doubles, row i for shots_dev[i]:
+ *                   column k = the Born probability of outcome 1 (FP64) of the shot's readout k
+ *                   (M and R instructions numbered in text order); NaN where the shot ended before
+ *                   reaching readout k.  Caller-owned; filled by the call.
+ *   readout_k       columns of readout_p1_dev (0 = no record)
+ *   sweep_cap       > 0: Jacobi sweep limit of every split of the shots (default 40 for QC_C64, 60
+ *                   for QC_C128); a split that does not converge within it ends its shot with
+ *                   per-shot status QC_ENOCONV.  The noiseless reference run keeps the default. */
+typedef struct {
+    double* readout_p1_dev;
+    int32_t readout_k;
+    int32_t sweep_cap;
+} qc_mps_trace;
+
+/* mps_sample_batch with the verification hooks above (trace may be NULL, which is mps_sample_batch). */
+qc_status mps_sample_batch_traced(const qc_circuit* circuit, qc_noise noise, const uint64_t* shots_dev,
+                                  uint64_t nshots, qc_mps_params params, qc_counts* per_w,
+                                  int32_t w_max, qc_shot_result* per_shot_dev,
+                                  const qc_mps_trace* trace, void* stream);
+
 /* Bytes of device memory one in-flight shot needs (site tensors at their capacities plus the
  * per-shot split scratch), the footprint used for admission. */
 qc_status mps_shot_footprint(const qc_circuit* circuit, qc_mps_params params, uint64_t* bytes);
+
+/* ---- measurement support (no counterpart in the paper) -------------------------------------- */
+
+/* Issue rates of the current device's arithmetic units, the denominators of the rooflines of the
+ * MPS engine (FP32) and of the pre-screen (32-bit integer logic).  Each rate comes from a kernel of
+ * long independent chains of one instruction on every SM (4 CTAs x 256 threads per SM, 8 chains per
+ * thread), the best of three launches timed with CUDA events on `stream`; it takes ~50 ms.
+ *   ffma_tflops   FP32 fused multiply-add, 2 flops each
+ *   ffma2_tflops  paired FP32 fused multiply-add (two lanes of a 64-bit register), 4 flops each
+ *   dfma_tflops   FP64 fused multiply-add, 2 flops each
+ *   lop3_tops     32-bit three-input logic operations (1e12 per second)
+ *   imad_tops     32-bit integer multiply-adds (1e12 per second)
+ *   sm_count, sm_clock_mhz  from the device attributes (the clock is the maximum SM clock) */
+typedef struct {
+    int32_t sm_count;
+    double sm_clock_mhz;
+    double ffma_tflops, ffma2_tflops, dfma_tflops, lop3_tops, imad_tops;
+} qc_alu_peaks;
+qc_status qc_measure_alu_peaks(qc_alu_peaks* out, void* stream);
 
 /* ---- serving loop ---------------------------------------------------------------------- */
 
@@ -220,12 +264,18 @@ typedef struct {
     uint64_t survivors;         /* shots kept by the pre-screen */
     qc_counts counts[16];       /* per fault weight, bin 15 collects w >= 15 */
     double submit_ms, start_ms, end_ms; /* on the server's clock */
+    char error[224];            /* when state < 0: the failing call's message (NUL-terminated) */
 } qc_job_result;
 
-/* Start a request loop on the current device.  Jobs are admitted while their in-flight
- * footprint fits the budget, are pre-screened, and their surviving shots are simulated in
- * batches that mix the shots of all admitted jobs; a finished batch slot is back-filled from
- * the queue.  *out is owned by the library; release with mps_serve_destroy. */
+/* Start a request loop on the current device.  Jobs are pre-screened as they arrive; their
+ * surviving shots are cut into chunks of at most 512 shots, and n_streams worker threads each
+ * launch one chunk at a time as its own persistent engine batch on their own stream, so chunks
+ * of different jobs overlap on the device (each batch holds the shots of one job; inside it a
+ * finished shot slot is back-filled with the next shot).  A chunk is launched only while its
+ * footprint (slots x bytes of one slot of the capacity bucket the engine allocates) fits the
+ * budget next to the chunks in flight.  Chunks go to the job with the smallest remaining work
+ * divided by 1 + age/1 s (age since submission); jobs older than 2 s go first, oldest first.
+ * *out is owned by the library; release with mps_serve_destroy. */
 qc_status mps_serve_create(const qc_serve_cfg* cfg, qc_server** out);
 /* Queue nshots shots [shot0, shot0 + nshots) of a circuit (shot0 a multiple of 64).  The circuit
  * must stay alive until the job is done or cancelled. */

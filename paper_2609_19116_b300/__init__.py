@@ -4,5 +4,5 @@ The sampling path runs in the CUDA library libqcmps.so (include/qcmps.h); this p
 binds it.  Importing it does not touch the GPU.
 """
 from ._native import QC_C64, QC_C128, QcError  # noqa: F401
-from .api import (Circuit, Server, mps_sample_batch, pauli_prescreen, qc_sample_faults,  # noqa: F401
-                  SHOT_DTYPE)
+from .api import (Circuit, Server, mps_sample_batch, mps_sample_batch_traced, pauli_prescreen,  # noqa: F401
+                  qc_sample_faults, measure_alu_peaks, SHOT_DTYPE)

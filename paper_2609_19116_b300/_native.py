@@ -49,7 +49,18 @@ class ShotResult(C.Structure):
     _fields_ = [("shot", C.c_uint64), ("status", C.c_int32), ("weight", C.c_int32),
                 ("logical_error", C.c_int32), ("chi_peak", C.c_int32), ("abort_op", C.c_int64),
                 ("fidelity", C.c_double), ("discarded", C.c_double), ("degenerate_cuts", C.c_int32),
-                ("n_updates", C.c_int32), ("sweeps", C.c_int32), ("alg_flops", C.c_double)]
+                ("n_updates", C.c_int32), ("sweeps", C.c_int32), ("alg_flops", C.c_double),
+                ("gmem_updates", C.c_int32), ("reserved", C.c_int32)]
+
+
+class MpsTrace(C.Structure):
+    _fields_ = [("readout_p1_dev", C.c_void_p), ("readout_k", C.c_int32), ("sweep_cap", C.c_int32)]
+
+
+class AluPeaks(C.Structure):
+    _fields_ = [("sm_count", C.c_int32), ("sm_clock_mhz", C.c_double), ("ffma_tflops", C.c_double),
+                ("ffma2_tflops", C.c_double), ("dfma_tflops", C.c_double), ("lop3_tops", C.c_double),
+                ("imad_tops", C.c_double)]
 
 
 class ServeCfg(C.Structure):
@@ -59,7 +70,7 @@ class ServeCfg(C.Structure):
 class JobResult(C.Structure):
     _fields_ = [("state", C.c_int32), ("shots", C.c_uint64), ("survivors", C.c_uint64),
                 ("counts", Counts * 16), ("submit_ms", C.c_double), ("start_ms", C.c_double),
-                ("end_ms", C.c_double)]
+                ("end_ms", C.c_double), ("error", C.c_char * 224)]
 
 
 _lib = None
@@ -84,7 +95,10 @@ def lib():
             "pauli_prescreen_noalloc": (C.c_int, [vp, Noise, u64, u64, vp, vp, u64, C.POINTER(u64), vp, vp, i32,
                                                   vp]),
             "mps_sample_batch": (C.c_int, [vp, Noise, vp, u64, MpsParams, vp, i32, vp, vp]),
+            "mps_sample_batch_traced": (C.c_int, [vp, Noise, vp, u64, MpsParams, vp, i32, vp,
+                                                  C.POINTER(MpsTrace), vp]),
             "mps_shot_footprint": (C.c_int, [vp, MpsParams, C.POINTER(u64)]),
+            "qc_measure_alu_peaks": (C.c_int, [C.POINTER(AluPeaks), vp]),
             "mps_serve_create": (C.c_int, [C.POINTER(ServeCfg), C.POINTER(vp)]),
             "mps_serve_submit": (C.c_int, [vp, vp, Noise, MpsParams, u64, u64, C.POINTER(u64)]),
             "mps_serve_poll": (C.c_int, [vp, u64, C.POINTER(JobResult)]),
@@ -106,5 +120,5 @@ def check(status: int):
 
 
 EXPORTED = ("qc_last_error", "qc_circuit_parse", "qc_circuit_free", "qc_circuit_get_info", "qc_circuit_decided",
-            "qc_sample_faults", "pauli_prescreen", "pauli_prescreen_noalloc", "mps_sample_batch", "mps_shot_footprint", "mps_serve_create",
+            "qc_sample_faults", "pauli_prescreen", "pauli_prescreen_noalloc", "mps_sample_batch", "mps_sample_batch_traced", "mps_shot_footprint", "qc_measure_alu_peaks", "mps_serve_create",
             "mps_serve_submit", "mps_serve_poll", "mps_serve_cancel", "mps_serve_destroy")

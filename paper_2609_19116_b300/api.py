@@ -14,7 +14,8 @@ from . import _native as N
 
 SHOT_DTYPE = np.dtype([("shot", "<u8"), ("status", "<i4"), ("weight", "<i4"), ("logical_error", "<i4"),
                        ("chi_peak", "<i4"), ("abort_op", "<i8"), ("fidelity", "<f8"), ("discarded", "<f8"),
-                       ("degenerate_cuts", "<i4"), ("n_updates", "<i4"), ("sweeps", "<i4"), ("alg_flops", "<f8")], align=True)
+                       ("degenerate_cuts", "<i4"), ("n_updates", "<i4"), ("sweeps", "<i4"), ("alg_flops", "<f8"),
+                       ("gmem_updates", "<i4"), ("reserved", "<i4")], align=True)
 assert SHOT_DTYPE.itemsize == C.sizeof(N.ShotResult)
 
 
@@ -133,6 +134,34 @@ def mps_sample_batch(circ: Circuit, shots: torch.Tensor, *, p: float, seed: int,
     return arr, res
 
 
+def mps_sample_batch_traced(circ: Circuit, shots: torch.Tensor, *, p: float, seed: int, chi_max: int, cutoff: float,
+                            precision: int = N.QC_C64, tau: float = 0.0, w_max: int = 15, fault_weight: int = -1,
+                            readout_k: int = 0, sweep_cap: int = 0, stream=None):
+    """mps_sample_batch with the verification hooks: returns (counts, per-shot results, readout
+    probabilities [nshots, readout_k] as a float64 numpy array, NaN after a shot's end)."""
+    shots = _dev_u64(shots)
+    n = shots.numel()
+    counts = (N.Counts * (w_max + 1))()
+    buf = torch.zeros(max(n, 1) * SHOT_DTYPE.itemsize, dtype=torch.uint8, device=shots.device)
+    p1 = torch.empty(max(n * readout_k, 1), dtype=torch.float64, device=shots.device)
+    tr = N.MpsTrace(p1.data_ptr() if readout_k > 0 else None, readout_k, sweep_cap)
+    prm = N.MpsParams(chi_max, cutoff, precision, tau)
+    N.check(N.lib().mps_sample_batch_traced(circ.handle, N.Noise(p, seed, fault_weight), _ptr(shots), n, prm,
+                                            C.cast(counts, C.c_void_p), w_max, _ptr(buf), C.byref(tr),
+                                            _stream(stream)))
+    arr = np.array([[c.n, c.n_acc, c.n_err] for c in counts], dtype=np.uint64)
+    res = np.frombuffer(buf[: n * SHOT_DTYPE.itemsize].cpu().numpy().tobytes(), dtype=SHOT_DTYPE)
+    rec = p1[: n * readout_k].cpu().numpy().reshape(n, readout_k) if readout_k > 0 else None
+    return arr, res, rec
+
+
+def measure_alu_peaks(stream=None) -> dict:
+    """qc_measure_alu_peaks: measured FP32 / paired-FP32 / FP64 FMA and INT32 LOP3 / IMAD rates."""
+    r = N.AluPeaks()
+    N.check(N.lib().qc_measure_alu_peaks(C.byref(r), _stream(stream)))
+    return {k: getattr(r, k) for k, _ in N.AluPeaks._fields_}
+
+
 class Server:
     """The serving loop (mps_serve_create / submit / poll / cancel / destroy)."""
 
@@ -158,7 +187,8 @@ class Server:
             return None
         counts = np.array([[c.n, c.n_acc, c.n_err] for c in r.counts], dtype=np.uint64)
         return {"state": r.state, "shots": r.shots, "survivors": r.survivors, "counts": counts,
-                "submit_ms": r.submit_ms, "start_ms": r.start_ms, "end_ms": r.end_ms}
+                "submit_ms": r.submit_ms, "start_ms": r.start_ms, "end_ms": r.end_ms,
+                "error": r.error.decode(errors="replace")}
 
     def cancel(self, job_id: int):
         N.check(N.lib().mps_serve_cancel(self._h, job_id))

@@ -6,6 +6,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <set>
 #include <sstream>
 
 #include "qc_internal.h"
@@ -26,6 +27,38 @@ qc_status fail(qc_status st, const char* fmt, ...) {
 
 qc_status cuda_fail(cudaError_t e, const char* what) {
     return fail(QC_EDEVICE, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// A kernel's dynamic shared-memory limit is process-wide state of the device.  Setting it per call to
+// the size that call needs races with concurrent callers (a host thread that lowers it between another
+// thread's set and launch makes that launch fail), so it is raised once per (device, kernel) to the
+// device's opt-in maximum and never lowered; every launch then only asks for what it needs.
+qc_status smem_optin(const void* fn) {
+    static std::mutex mu;
+    static std::set<std::pair<int, const void*>> done;
+    int d = 0;
+    QC_CUDA(cudaGetDevice(&d));
+    std::lock_guard<std::mutex> lk(mu);
+    if (done.count({d, fn})) return QC_OK;
+    int optin = 0;
+    QC_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, d));
+    cudaFuncAttributes fa{};
+    QC_CUDA(cudaFuncGetAttributes(&fa, fn));
+    const int dyn = optin - (int)fa.sharedSizeBytes;
+    QC_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn));
+    done.insert({d, fn});
+    return QC_OK;
+}
+
+qc_status smem_limit(const void* fn, size_t* bytes) {
+    int d = 0;
+    QC_CUDA(cudaGetDevice(&d));
+    int optin = 0;
+    QC_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, d));
+    cudaFuncAttributes fa{};
+    QC_CUDA(cudaFuncGetAttributes(&fa, fn));
+    *bytes = (size_t)(optin - (int)fa.sharedSizeBytes);
+    return QC_OK;
 }
 
 Thresholds make_thresholds(double p) {

@@ -91,6 +91,9 @@ struct EngineParams {
     int* ref_dims_out;    // reference run: bond dims [nq+1]
     double* ref_disc_out;
     int sweep_cap;
+    double* trace_p1;          // optional [ntasks x trace_k]: readout probabilities of each shot
+    const uint64_t* trace_pos; // optional: record row of each task (the capacity re-run pass)
+    int trace_k;
 };
 
 template <typename R>
@@ -171,8 +174,10 @@ struct Engine {
     int64_t abort_op;
     unsigned long long flops;  // algorithmic flops of this shot (integer counts, thread 0)
     int sweeps;
+    int gmem_updates;          // two-site updates whose Jacobi matrix lived in global memory
 
     const int tid_;  // thread index within the engine (the warp lane in warp mode)
+    uint64_t task_ = 0;
 
     __device__ Engine(const EngineParams<R>& p, Shared<R>& s, int slot_id, int tid)
         : P(p), S(s), tid_(tid) {
@@ -630,6 +635,7 @@ struct Engine {
         const R floor2 = fl * fl * (R)frod;
         const int bw = (int)(P.x_smem / (2 * (uint32_t)(rows + 1)));
         const bool blocked = (X == xg) && bw >= 2 && bw * 2 < cols;
+        gmem_updates += (X == xg) ? 1 : 0;
         if (!(blocked ? jacobi_blocked(X, rows, cols, ld, floor2, S.X, bw) : jacobi(X, rows, cols, ld, floor2))) {
             status = QC_ENOCONV;
             release_big(locked);
@@ -1078,6 +1084,10 @@ struct Engine {
         if (tid_ == 0) reset_pend(q);
         const double tot = p0 + p1;
         const double pr1 = tot > 0 ? p1 / tot : 0.0;
+        if (P.trace_p1 && !P.reference && rid < (uint32_t)P.trace_k && tid_ == 0) {
+            const uint64_t row = P.trace_pos ? P.trace_pos[task_] : task_;
+            P.trace_p1[row * (uint64_t)P.trace_k + rid] = pr1;
+        }
         int outcome;
         if (P.reference) {
             if (is_meas) {
@@ -1231,8 +1241,10 @@ struct Engine {
     }
 
     __device__ void run(uint64_t task) {
+        task_ = task;
         const uint64_t shot = P.reference ? 0 : P.shots[task];
         status = 0; disc = 0; degen = 0; chi_peak = 1; nupd = 0; abort_op = -1; flops = 0; sweeps = 0;
+        gmem_updates = 0;
         for (int q = tid_; q <= P.nq; q += NT) S.dims[q] = 1;
         for (int q = tid_; q < P.nq; q += NT) {
             V* a = site(q);
@@ -1340,6 +1352,7 @@ struct Engine {
                     res.n_updates = nupd;
                     res.alg_flops = (double)flops;
                     res.sweeps = sweeps;
+                    res.gmem_updates = gmem_updates;
                     P.per_shot[task] = res;
                 }
             }
@@ -1508,6 +1521,27 @@ static SlotLayout slot_layout(int n, int chi_max) {
     return L;
 }
 
+// Elements of one slot's split scratch for slots of capacity chi next to a reference state whose largest
+// bond is ref_chi: the Jacobi / overlap work area X, the theta' copy, and the singular values with their
+// order.  Used for the allocation and for the admission footprint, so both always agree.
+static uint64_t scratch_elems(int chi, int ref_chi, size_t sizeR, size_t sizeV) {
+    const uint64_t cap2 = (uint64_t)std::max(chi, ref_chi);
+    const uint64_t x_full = (uint64_t)(2 * chi + 1) * (2 * chi);
+    const uint64_t xg_elems = std::max(x_full, cap2 * cap2 * 3);
+    const uint64_t sg_elems = ((uint64_t)(2 * chi) * (sizeR + sizeof(int)) + sizeV - 1) / sizeV + 2;
+    return xg_elems + (uint64_t)(2 * chi) * (2 * chi) + sg_elems;
+}
+
+// Capacity bucket of the first pass: the smallest power of two >= max(64, 2 x the reference's chi_peak),
+// at most the full capacity chi (QCMPS_CHI_ALLOC overrides it for tests and tuning).
+static int bucket_chi(int ref_chi_peak, int chi) {
+    int chi_alloc = 64;
+    while (chi_alloc < 2 * ref_chi_peak) chi_alloc *= 2;
+    chi_alloc = std::min(chi_alloc, chi);
+    if (const char* ca = getenv("QCMPS_CHI_ALLOC")) chi_alloc = std::max(1, std::min(chi, atoi(ca)));
+    return chi_alloc;
+}
+
 // Shared-memory configuration of one engine variant: how much of theta's Jacobi matrix X fits in
 // shared memory next to the fixed per-CTA arrays, within the variant's budget.
 template <typename R, int NT>
@@ -1533,8 +1567,7 @@ static qc_status run_pass(CircuitImpl& c, EngineParams<R> P, const SlotLayout& L
     const uint64_t x_full = (uint64_t)(2 * chi + 1) * (2 * chi);
     const uint64_t over_full = cap2 * cap2 * 3;
     const uint64_t xg_elems = std::max(x_full, over_full);
-    const uint64_t sg_elems = ((uint64_t)(2 * chi) * (sizeof(R) + sizeof(int)) + sizeof(V) - 1) / sizeof(V) + 2;
-    const uint64_t scratch_stride = xg_elems + (uint64_t)(2 * chi) * (2 * chi) + sg_elems;
+    const uint64_t scratch_stride = scratch_elems(chi, P.ref_chi, sizeof(R), sizeof(V));
     P.slot_stride = L.stride;
     P.scratch_stride = scratch_stride;
     P.xg_elems = xg_elems;
@@ -1585,7 +1618,10 @@ static qc_status run_pass(CircuitImpl& c, EngineParams<R> P, const SlotLayout& L
         fn = (const void*)engine_kernel<R, NT_BIG>;
         nt = NT_BIG;
     }
-    QC_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    {
+        const qc_status so = smem_optin(fn);
+        if (so != QC_OK) return so;
+    }
     int per_sm = 0;
     QC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, nt, smem));
     if (per_sm < 1) return fail(QC_ENOMEM, "engine does not fit on an SM (smem %zu)", smem);
@@ -1641,7 +1677,8 @@ static qc_status run_pass(CircuitImpl& c, EngineParams<R> P, const SlotLayout& L
 template <typename R, int NT_BIG>
 static qc_status run_engine(CircuitImpl& c, qc_noise noise, const uint64_t* shots_dev, uint64_t nshots,
                             qc_mps_params prm, unsigned long long* counts_dev, int wmax,
-                            qc_shot_result* per_shot, cudaStream_t s, int max_slots, bool shared_gpu) {
+                            qc_shot_result* per_shot, cudaStream_t s, int max_slots, bool shared_gpu,
+                            const qc_mps_trace* trace) {
     using V = typename VecOf<R>::T;
     DeviceCopy* dc;
     qc_status st = c.device_copy(&dc);
@@ -1684,7 +1721,7 @@ static qc_status run_engine(CircuitImpl& c, qc_noise noise, const uint64_t* shot
     P.tau = prm.tau;
     P.precision = prm.precision;
     P.wmax = wmax;
-    P.sweep_cap = sizeof(R) == 4 ? 40 : 60;
+    P.sweep_cap = sizeof(R) == 4 ? 40 : 60;  // the noiseless reference run always keeps the default
     {
         int center = 0;
         for (const MpsOp& o : c.mps) {
@@ -1711,17 +1748,17 @@ static qc_status run_engine(CircuitImpl& c, qc_noise noise, const uint64_t* shot
             if (e == cudaSuccess) e = cudaMalloc(&rs.dims, (c.n + 1) * sizeof(int));
             if (e == cudaSuccess) e = cudaMalloc(&rs.cap, (c.n + 1) * sizeof(int));
             if (e == cudaSuccess) e = cudaMalloc(&rs.off, (c.n + 1) * sizeof(uint64_t));
-            if (e == cudaSuccess) e = cudaMalloc(&tmp, tmp_bytes);
+            if (e == cudaSuccess) e = cudaMallocAsync((void**)&tmp, tmp_bytes, s);
             if (e == cudaSuccess) e = cudaMemcpy(rs.cap, L.cap.data(), (c.n + 1) * sizeof(int), cudaMemcpyHostToDevice);
             if (e == cudaSuccess) e = cudaMemcpy(rs.off, L.off.data(), (c.n + 1) * sizeof(uint64_t), cudaMemcpyHostToDevice);
-            if (e == cudaSuccess) e = cudaMemset(tmp, 0, 64);
+            if (e == cudaSuccess) e = cudaMemsetAsync(tmp, 0, 64, s);
             qc_status out = QC_OK;
             if (e != cudaSuccess) out = cuda_fail(e, "reference workspace");
             if (out == QC_OK) {
                 EngineParams<R> Pr = P;
                 Pr.x_big = 0;
                 const size_t smem = configure_smem<R, NT_BIG>(Pr, 200 * 1024, std::max(x_full, over_full));
-                e = cudaFuncSetAttribute(engine_kernel<R, NT_BIG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                if (smem_optin((const void*)engine_kernel<R, NT_BIG>) != QC_OK) e = cudaErrorInvalidValue;
                 Pr.reference = 1;
                 Pr.mps = reinterpret_cast<V*>(rs.state);
                 Pr.off = rs.off;
@@ -1764,7 +1801,7 @@ static qc_status run_engine(CircuitImpl& c, qc_noise noise, const uint64_t* shot
                     rs.norm = nn;
                 }
             }
-            cudaFree(tmp);
+            if (tmp) cudaFreeAsync(tmp, s);
             if (out != QC_OK) {
                 cudaFree(rs.state); cudaFree(rs.dims); cudaFree(rs.cap); cudaFree(rs.off);
                 return out;
@@ -1774,13 +1811,15 @@ static qc_status run_engine(CircuitImpl& c, qc_noise noise, const uint64_t* shot
         ref = &it->second;
     }
     if (nshots == 0) return QC_OK;
+    if (trace && trace->sweep_cap > 0) P.sweep_cap = trace->sweep_cap;
+    if (trace && trace->readout_p1_dev && trace->readout_k > 0) {
+        P.trace_p1 = trace->readout_p1_dev;
+        P.trace_k = trace->readout_k;
+    }
 
     // 2. capacity bucket: slots sized for chi_alloc = min(chi, max(64, 2 chi_peak_ref)); a shot
     //    that outgrows it is reported by the first pass and re-run with full capacity
-    int chi_alloc = 64;
-    while (chi_alloc < 2 * ref->chi_peak) chi_alloc *= 2;
-    chi_alloc = std::min(chi_alloc, chi);
-    if (const char* ca = getenv("QCMPS_CHI_ALLOC")) chi_alloc = std::max(1, std::min(chi, atoi(ca)));
+    const int chi_alloc = bucket_chi(ref->chi_peak, chi);
     if (chi_alloc >= chi)
         return run_pass<R, NT_BIG>(c, P, L, ref->state, ref->cap, ref->off, *ref, shots_dev, nshots, counts_dev,
                                    per_shot, s, max_slots, nsm, false);
@@ -1825,13 +1864,19 @@ static qc_status run_engine(CircuitImpl& c, qc_noise noise, const uint64_t* shot
     if (out == QC_OK && !redo.empty()) {
         // second pass with the full capacity, then the records go back to their places
         uint64_t* shots2 = nullptr;
+        uint64_t* pos2 = nullptr;
         qc_shot_result* res2 = nullptr;
         cudaError_t e = cudaMallocAsync((void**)&shots2, redo.size() * sizeof(uint64_t), s);
         if (e == cudaSuccess) e = cudaMallocAsync((void**)&res2, redo.size() * sizeof(qc_shot_result), s);
+        if (e == cudaSuccess && P.trace_p1) e = cudaMallocAsync((void**)&pos2, where.size() * sizeof(uint64_t), s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(shots2, redo.data(), redo.size() * sizeof(uint64_t), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess && pos2)
+            e = cudaMemcpyAsync(pos2, where.data(), where.size() * sizeof(uint64_t), cudaMemcpyHostToDevice, s);
         if (e != cudaSuccess) out = cuda_fail(e, "second pass");
+        EngineParams<R> P2 = P;
+        P2.trace_pos = pos2;
         if (out == QC_OK)
-            out = run_pass<R, NT_BIG>(c, P, L, ref->state, ref->cap, ref->off, *ref, shots2, redo.size(), counts_dev,
+            out = run_pass<R, NT_BIG>(c, P2, L, ref->state, ref->cap, ref->off, *ref, shots2, redo.size(), counts_dev,
                                       res2, s, max_slots, nsm, false);
         if (out == QC_OK && per_shot) {
             std::vector<qc_shot_result> h2(redo.size());
@@ -1844,6 +1889,7 @@ static qc_status run_engine(CircuitImpl& c, qc_noise noise, const uint64_t* shot
         }
         cudaFreeAsync(shots2, s);
         cudaFreeAsync(res2, s);
+        if (pos2) cudaFreeAsync(pos2, s);
     }
     if (res1 != per_shot) cudaFreeAsync(res1, s);
     return out;
@@ -1851,7 +1897,7 @@ static qc_status run_engine(CircuitImpl& c, qc_noise noise, const uint64_t* shot
 
 qc_status engine_launch(CircuitImpl& c, qc_noise noise, const uint64_t* shots_dev, uint64_t nshots,
                         qc_mps_params prm, unsigned long long* counts_dev, int wmax, qc_shot_result* per_shot,
-                        cudaStream_t s, int max_slots, bool shared_gpu) {
+                        cudaStream_t s, int max_slots, bool shared_gpu, const qc_mps_trace* trace) {
     if (!(noise.p >= 0.0 && noise.p < 1.0)) return fail(QC_EINVAL, "p must lie in [0, 1)");
     if (prm.chi_max < 1) return fail(QC_EINVAL, "chi_max must be >= 1");
     if (!(prm.cutoff >= 0.0)) return fail(QC_EINVAL, "cutoff must be >= 0");
@@ -1863,9 +1909,9 @@ qc_status engine_launch(CircuitImpl& c, qc_noise noise, const uint64_t* shots_de
     if (c.n < 2) return fail(QC_EINVAL, "the MPS engine needs at least two qubits");
     if (prm.precision == QC_C64)
         return run_engine<float, NT_F>(c, noise, shots_dev, nshots, prm, counts_dev, wmax, per_shot, s, max_slots,
-                                       shared_gpu);
+                                       shared_gpu, trace);
     return run_engine<double, NT_D>(c, noise, shots_dev, nshots, prm, counts_dev, wmax, per_shot, s, max_slots,
-                                    shared_gpu);
+                                    shared_gpu, trace);
 }
 
 qc_status shot_footprint(const CircuitImpl& c, qc_mps_params prm, uint64_t* bytes) {
@@ -1882,20 +1928,50 @@ qc_status shot_footprint(const CircuitImpl& c, qc_mps_params prm, uint64_t* byte
 
 using namespace qc;
 
-extern "C" qc_status mps_sample_batch(const qc_circuit* circuit, qc_noise noise, const uint64_t* shots_dev,
-                                      uint64_t nshots, qc_mps_params params, qc_counts* per_w, int32_t w_max,
-                                      qc_shot_result* per_shot_dev, void* stream) {
+namespace qc {
+qc_status bucket_footprint(CircuitImpl& c, qc_noise noise, qc_mps_params prm, cudaStream_t s, uint64_t* bytes) {
+    // the reference run (cached) tells the bucket; nshots = 0 computes it and launches nothing else
+    qc_status st = engine_launch(c, noise, nullptr, 0, prm, nullptr, 0, nullptr, s, 0, true);
+    if (st != QC_OK) return st;
+    int dev = 0;
+    QC_CUDA(cudaGetDevice(&dev));
+    int ref_chi = 1;
+    {
+        std::lock_guard<std::mutex> lk(c.ref_mu);
+        auto it = c.refs.find(RefKey{dev, prm.chi_max, prm.precision, prm.cutoff});
+        if (it == c.refs.end()) return fail(QC_EDEVICE, "reference state missing after the reference run");
+        ref_chi = std::max(1, it->second.chi_peak);
+    }
+    const int chi = slot_layout(c.n, prm.chi_max).chi_cap;
+    const int chi_alloc = bucket_chi(ref_chi, chi);
+    const SlotLayout L1 = slot_layout(c.n, chi_alloc);
+    const bool c128 = prm.precision == QC_C128;
+    const uint64_t es = c128 ? 16 : 8;
+    *bytes = (L1.stride + scratch_elems(chi_alloc, ref_chi, c128 ? 8 : 4, es)) * es;
+    return QC_OK;
+}
+}  // namespace qc
+
+extern "C" qc_status mps_sample_batch_traced(const qc_circuit* circuit, qc_noise noise, const uint64_t* shots_dev,
+                                             uint64_t nshots, qc_mps_params params, qc_counts* per_w, int32_t w_max,
+                                             qc_shot_result* per_shot_dev, const qc_mps_trace* trace, void* stream) {
     if (!circuit) return fail(QC_EINVAL, "null circuit");
     if (w_max < 0 || w_max > 4095) return fail(QC_EINVAL, "w_max must lie in [0, 4095]");
+    if (trace && trace->readout_k < 0) return fail(QC_EINVAL, "readout_k must be >= 0");
+    if (trace && trace->readout_k > 0 && nshots && !trace->readout_p1_dev)
+        return fail(QC_EINVAL, "null readout record buffer");
     cudaStream_t s = (cudaStream_t)stream;
     CircuitImpl& c = const_cast<qc_circuit*>(circuit)->impl;
+    if (trace && trace->readout_p1_dev && trace->readout_k > 0 && nshots)  // all-ones bytes: NaN
+        QC_CUDA(cudaMemsetAsync(trace->readout_p1_dev, 0xFF, nshots * (size_t)trace->readout_k * sizeof(double), s));
     unsigned long long* counts = nullptr;
     const size_t cb = 3 * (size_t)(w_max + 1) * sizeof(unsigned long long);
     QC_CUDA(cudaMallocAsync((void**)&counts, cb, s));
     qc_status st = QC_OK;
     cudaError_t e = cudaMemsetAsync(counts, 0, cb, s);
     if (e != cudaSuccess) st = cuda_fail(e, "memset");
-    if (st == QC_OK) st = engine_launch(c, noise, shots_dev, nshots, params, counts, w_max, per_shot_dev, s, 0, false);
+    if (st == QC_OK)
+        st = engine_launch(c, noise, shots_dev, nshots, params, counts, w_max, per_shot_dev, s, 0, false, trace);
     if (st == QC_OK) {
         std::vector<unsigned long long> h(3 * (w_max + 1));
         e = cudaMemcpyAsync(h.data(), counts, cb, cudaMemcpyDeviceToHost, s);
@@ -1910,6 +1986,13 @@ extern "C" qc_status mps_sample_batch(const qc_circuit* circuit, qc_noise noise,
     }
     cudaFreeAsync(counts, s);
     return st;
+}
+
+extern "C" qc_status mps_sample_batch(const qc_circuit* circuit, qc_noise noise, const uint64_t* shots_dev,
+                                      uint64_t nshots, qc_mps_params params, qc_counts* per_w, int32_t w_max,
+                                      qc_shot_result* per_shot_dev, void* stream) {
+    return mps_sample_batch_traced(circuit, noise, shots_dev, nshots, params, per_w, w_max, per_shot_dev, nullptr,
+                                   stream);
 }
 
 extern "C" qc_status mps_shot_footprint(const qc_circuit* circuit, qc_mps_params params, uint64_t* bytes) {

@@ -525,8 +525,8 @@ qc_status prescreen_run(CircuitImpl& c, qc_noise noise, uint64_t shot0, uint64_t
         const size_t smem = 2ull * c.n * PRE_THREADS * sizeof(uint64_t) + PRE_CHUNK * sizeof(PreOp) +
                             64 * sizeof(uint32_t) + 2 * WMAX_BINS * sizeof(unsigned long long);
         if (smem > 227 * 1024) { out = fail(QC_EINVAL, "too many qubits for the pre-screen frame (%d)", c.n); break; }
-        e = cudaFuncSetAttribute(prescreen_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) { out = cuda_fail(e, "cudaFuncSetAttribute"); break; }
+        out = smem_optin((const void*)prescreen_kernel);
+        if (out != QC_OK) break;
         if (noise.fault_weight >= 0) {
             e = cudaMemsetAsync(kept_mask_dev, 0, nwords * sizeof(uint64_t), s);
             if (e != cudaSuccess) { out = cuda_fail(e, "memset"); break; }
@@ -574,9 +574,9 @@ extern "C" qc_status pauli_prescreen(const qc_circuit* circuit, qc_noise noise, 
 }
 
 // ---- pre-screen variant for callers that cannot allocate device memory ------------------------
-// Some callers cannot call cudaMalloc at all: code running inside a region that forbids
-// allocation (a CUDA-graph capture they do not control, a memory-pool-locked serving process with
-// a fixed device-memory budget, an embedding runtime that owns every allocation).  This variant
+// Some callers cannot call cudaMalloc at all: a serving process whose device memory is a fixed pool
+// with a locked budget, or an embedding runtime that owns every allocation.  (The call copies its
+// counts to host memory and synchronises the stream, so it does not belong inside a stream capture.)  This variant
 // keeps all of its scratch -- the staged frame program, the per-weight histograms and the
 // compaction offsets -- in one file-scope device array instead of allocating it.  The array is
 // part of the library image: every GPU that loads the library holds it until the process exits.
@@ -673,7 +673,8 @@ extern "C" qc_status pauli_prescreen_noalloc(const qc_circuit* circuit, qc_noise
     P.kept = kept_mask_dev;
     P.hist_drawn = reinterpret_cast<unsigned long long*>(hist);
     P.hist_kept = P.hist_drawn + WMAX_BINS;
-    QC_CUDA(cudaFuncSetAttribute(prescreen_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    st = smem_optin((const void*)prescreen_kernel);
+    if (st != QC_OK) return st;
     prescreen_kernel<<<(unsigned)((nwords + PRE_THREADS - 1) / PRE_THREADS), PRE_THREADS, smem, s>>>(P);
     QC_CUDA(cudaGetLastError());
     compact_count<<<(unsigned)nchunks, CMP_THREADS, 0, s>>>(kept_mask_dev, nwords, chunk);

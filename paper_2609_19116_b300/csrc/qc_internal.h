@@ -108,6 +108,11 @@ struct CircuitImpl {
 // Error reporting (thread-local message).
 qc_status fail(qc_status st, const char* fmt, ...);
 qc_status cuda_fail(cudaError_t e, const char* what);
+// Raise a kernel's dynamic shared-memory limit to the device's opt-in maximum, once per (device,
+// kernel), so that concurrent launches with different sizes never race on the attribute.
+qc_status smem_optin(const void* fn);
+// The dynamic shared memory a launch of fn may ask for on the current device.
+qc_status smem_limit(const void* fn, size_t* bytes);
 #define QC_CUDA(call)                                         \
     do {                                                      \
         cudaError_t e_ = (call);                              \
@@ -127,8 +132,11 @@ qc_status prescreen_run(CircuitImpl& c, qc_noise noise, uint64_t shot0, uint64_t
                         cudaStream_t s);
 qc_status engine_launch(CircuitImpl& c, qc_noise noise, const uint64_t* shots_dev, uint64_t nshots,
                         qc_mps_params prm, unsigned long long* counts_dev, int wmax, qc_shot_result* per_shot,
-                        cudaStream_t s, int max_slots, bool shared_gpu);
+                        cudaStream_t s, int max_slots, bool shared_gpu, const qc_mps_trace* trace = nullptr);
 qc_status shot_footprint(const CircuitImpl& c, qc_mps_params prm, uint64_t* bytes);
+// Bytes of one shot slot of the first pass (the capacity bucket the engine allocates), computing and
+// caching the noiseless reference state on `s` if needed.
+qc_status bucket_footprint(CircuitImpl& c, qc_noise noise, qc_mps_params prm, cudaStream_t s, uint64_t* bytes);
 
 // Pauli code conventions.
 #if defined(__CUDACC__)

@@ -1,16 +1,23 @@
 // Serving loop: sampling jobs for different circuits and noise rates arrive while others run.
 //
 // A job is pre-screened as a whole (Sec. 4.2), then its surviving shots are cut into chunks.
-// Worker threads, one per CUDA stream, take the next chunk of the admitted job with the least
-// remaining work, so chunks of different jobs run concurrently on the device; inside a chunk the persistent engine retires
-// rejected shots early and back-fills their slots (Sec. 4.3).  A chunk is launched only when its
-// in-flight footprint (slots x per-shot bytes) fits the HBM budget next to the chunks already
-// running; finished chunks release their share.  Latency is measured from submission to the end
-// of the job's last chunk.
+// Worker threads, one per CUDA stream, take the next chunk of the admitted job with the smallest
+// aged remaining work (remaining work divided by 1 + age / 1 s, age counted from submission; a job
+// older than 2 s goes before every younger one, oldest first), so small jobs do not queue behind
+// large ones and no job waits unboundedly: under any load a job is at most 2 s from being served
+// in submission order.  Chunks of different jobs run concurrently on the device, each as its
+// own persistent engine launch on its worker's stream; inside a chunk the engine retires rejected
+// shots early and back-fills their slots (Sec. 4.3).  A chunk is launched only when its in-flight
+// footprint (slots x bytes of one slot of the capacity bucket the engine allocates) fits the HBM
+// budget next to the chunks already running; finished chunks release their share.  Job buffers
+// are stream-ordered (cudaMallocAsync / cudaFreeAsync), so no worker synchronises the device.
+// Latency is measured from submission to the end of the job's last chunk.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
+#include <cstdio>
+#include <cstring>
 #include <deque>
 #include <thread>
 
@@ -35,10 +42,15 @@ struct Job {
     uint64_t next = 0;         // next survivor index to hand out
     uint64_t done = 0;         // survivors finished
     int inflight = 0;          // chunks running
+    int pending_error = QC_OK; // a failed chunk's status, reported once the job's other chunks end
     uint64_t footprint = 0;    // bytes per in-flight shot
     qc_counts counts[WBINS] = {};
     double submit_ms = 0, start_ms = -1, end_ms = -1;
+    char error[sizeof(((qc_job_result*)nullptr)->error)] = {};
 };
+
+constexpr double AGE_MS = 1000.0;      // remaining work is divided by 1 + age / AGE_MS
+constexpr double STARVE_MS = 2000.0;   // jobs older than this go first, oldest first
 
 }  // namespace
 
@@ -60,13 +72,20 @@ struct Server {
         return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     }
 
-    void finish(Job* j, int state) {
+    // Ends a job; its survivor buffer is released in stream order on `s` when a worker finishes it
+    // (every chunk reading it has completed on its own stream by then), else synchronously.
+    void finish(Job* j, int state, cudaStream_t s = nullptr, bool have_stream = false) {
         j->state = state;
         j->end_ms = now_ms();
         if (j->surv_dev) {
-            cudaFree(j->surv_dev);
+            if (have_stream) cudaFreeAsync(j->surv_dev, s);
+            else cudaFree(j->surv_dev);
             j->surv_dev = nullptr;
         }
+    }
+
+    static void note_error(Job* j) {
+        if (!j->error[0]) snprintf(j->error, sizeof j->error, "%s", qc_last_error());
     }
 
     // Pick work under the lock: a job to pre-screen (admission order; it is cheap and tells the
@@ -75,8 +94,10 @@ struct Server {
     // work = survivors not yet handed out x the circuit's site operations per shot.
     bool pick(Job*& job, bool& pre, uint64_t& first, uint64_t& count, uint64_t& bytes) {
         const uint64_t free_b = cfg.hbm_budget_bytes > inflight_bytes ? cfg.hbm_budget_bytes - inflight_bytes : 0;
+        const double now = now_ms();
         Job* best = nullptr;
-        double best_work = 0;
+        double best_score = 0;
+        bool best_starved = false;
         uint64_t best_slots = 0;
         for (Job* j : order) {
             if (j->state != QC_PENDING || j->cancelled) continue;
@@ -92,10 +113,16 @@ struct Server {
             uint64_t slots = std::min<uint64_t>(n, (uint64_t)max_slots);
             const uint64_t fit = j->footprint ? free_b / j->footprint : slots;
             if (fit == 0) continue;  // wait until memory frees up
+            const double age = now - j->submit_ms;
+            const bool starved = age > STARVE_MS;
+            // aged shortest-remaining-work: small jobs first, but age shrinks a job's score, and a job
+            // past the starvation bound goes before every job that is not (oldest first among those)
             const double work = (double)avail * (double)std::max<int64_t>(1, j->circ->n_updates);
-            if (!best || work < best_work) {
+            const double score = starved ? -age : work / (1.0 + age / AGE_MS);
+            if (!best || (starved && !best_starved) || (starved == best_starved && score < best_score)) {
                 best = j;
-                best_work = work;
+                best_score = score;
+                best_starved = starved;
                 best_slots = std::min(slots, fit);
             }
         }
@@ -109,7 +136,7 @@ struct Server {
         j->next += n;
         j->inflight += 1;
         inflight_bytes += bytes;
-        if (j->start_ms < 0) j->start_ms = now_ms();
+        if (j->start_ms < 0) j->start_ms = now;
         return true;
     }
 
@@ -134,29 +161,31 @@ struct Server {
                 uint64_t* mask = nullptr;
                 uint64_t* surv = nullptr;
                 qc_status st = QC_OK;
-                if (cudaMalloc(&mask, std::max<uint64_t>(nwords, 1) * 8) != cudaSuccess ||
-                    cudaMalloc(&surv, std::max<uint64_t>(j->nshots, 1) * 8) != cudaSuccess)
-                    st = fail(QC_ENOMEM, "job buffers");
+                if (cudaMallocAsync((void**)&mask, std::max<uint64_t>(nwords, 1) * 8, s) != cudaSuccess ||
+                    cudaMallocAsync((void**)&surv, std::max<uint64_t>(j->nshots, 1) * 8, s) != cudaSuccess)
+                    st = fail(QC_ENOMEM, "job buffers of %llu shots", (unsigned long long)j->nshots);
                 qc_survivors sv{surv, j->nshots, 0};
                 uint64_t hd[WBINS] = {}, hk[WBINS] = {};
                 if (st == QC_OK)
                     st = prescreen_run(*j->circ, j->noise, j->shot0, j->nshots, mask, &sv, hd, hk, WBINS - 1, s);
+                // admission charges one slot of the capacity bucket the engine will allocate
                 uint64_t fp = 0;
-                if (st == QC_OK) st = shot_footprint(*j->circ, j->prm, &fp);
-                cudaFree(mask);
+                if (st == QC_OK) st = bucket_footprint(*j->circ, j->noise, j->prm, s, &fp);
+                if (mask) cudaFreeAsync(mask, s);
                 std::lock_guard<std::mutex> lk(mu);
                 j->prescreening = false;
                 if (st != QC_OK) {
-                    cudaFree(surv);
-                    finish(j, st);
+                    note_error(j);
+                    if (surv) cudaFreeAsync(surv, s);
+                    finish(j, st, s, true);
                 } else {
                     j->prescreened = true;
                     j->surv_dev = surv;
                     j->survivors = sv.count;
                     j->footprint = fp;
                     for (int w = 0; w < WBINS; ++w) j->counts[w].n = hd[w];
-                    if (j->cancelled) finish(j, QC_ECANCELLED);
-                    else if (sv.count == 0) { if (j->start_ms < 0) j->start_ms = now_ms(); finish(j, QC_OK); }
+                    if (j->cancelled) finish(j, QC_ECANCELLED, s, true);
+                    else if (sv.count == 0) { if (j->start_ms < 0) j->start_ms = now_ms(); finish(j, QC_OK, s, true); }
                 }
                 cv.notify_all();
                 continue;
@@ -164,15 +193,18 @@ struct Server {
             // a chunk of survivors
             qc_status st = QC_OK;
             unsigned long long h[3 * WBINS] = {};
-            if (cudaMemsetAsync(counts, 0, sizeof h, s) != cudaSuccess) st = fail(QC_EDEVICE, "memset");
+            if (cudaMemsetAsync(counts, 0, sizeof h, s) != cudaSuccess) st = fail(QC_EDEVICE, "memset of the chunk counters");
             const int slots = (int)std::max<uint64_t>(1, bytes / std::max<uint64_t>(1, j->footprint));
             if (st == QC_OK)
                 st = engine_launch(*j->circ, j->noise, j->surv_dev + first, count, j->prm, counts, WBINS - 1, nullptr, s,
                                    slots, true);
-            if (st == QC_OK && (cudaMemcpyAsync(h, counts, sizeof h, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-                                cudaStreamSynchronize(s) != cudaSuccess))
-                st = fail(QC_EDEVICE, "engine chunk");
+            if (st == QC_OK) {
+                cudaError_t e = cudaMemcpyAsync(h, counts, sizeof h, cudaMemcpyDeviceToHost, s);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+                if (e != cudaSuccess) st = cuda_fail(e, "engine chunk");
+            }
             std::lock_guard<std::mutex> lk(mu);
+            if (st != QC_OK) note_error(j);
             inflight_bytes -= bytes;
             j->inflight -= 1;
             j->done += count;
@@ -181,9 +213,15 @@ struct Server {
                 j->counts[w].n_err += h[3 * w + 2];
             }
             if (j->state == QC_PENDING) {
-                if (st != QC_OK) finish(j, st);
-                else if (j->cancelled && j->inflight == 0) finish(j, QC_ECANCELLED);
-                else if (j->done == j->survivors && j->inflight == 0) finish(j, QC_OK);
+                // a failed chunk stops the job from handing out more chunks; the job ends with that
+                // status once no chunk of it is in flight (they still read its survivor buffer)
+                if (st != QC_OK && j->pending_error == QC_OK) j->pending_error = st;
+                if (j->pending_error != QC_OK) j->cancelled = true;
+                if (j->inflight == 0) {
+                    if (j->pending_error != QC_OK) finish(j, j->pending_error, s, true);
+                    else if (j->cancelled) finish(j, QC_ECANCELLED, s, true);
+                    else if (j->done == j->survivors) finish(j, QC_OK, s, true);
+                }
             }
             cv.notify_all();
         }
@@ -257,6 +295,8 @@ extern "C" qc_status mps_serve_poll(qc_server* server, uint64_t job_id, qc_job_r
     out->submit_ms = j->submit_ms;
     out->start_ms = j->start_ms;
     out->end_ms = j->end_ms;
+    memcpy(out->error, j->error, sizeof out->error);
+    out->error[sizeof out->error - 1] = 0;
     return QC_OK;
 }
 

@@ -90,3 +90,65 @@ def test_admission_budget_and_cancel():
         assert r2[j2]["state"] in (0, -6)
     finally:
         srv.close()
+
+
+def test_interleaved_mixed_jobs_all_complete():
+    """Many 17-qubit and 49-qubit jobs submitted back to back over 16 worker streams: their pre-screen
+    and engine launches need different shared-memory sizes and run concurrently; every job must end
+    with state 0 and the counts of the direct entry points."""
+    q = lib_ready()
+    c17 = q.Circuit(workload_circuit("d3_17q_12l", layers=6))
+    c49 = q.Circuit(workload_circuit("d5_49q_60l", layers=6))
+    jobs = []
+    for i in range(24):
+        c, chi = (c17, 32) if i % 2 == 0 else (c49, 128)
+        jobs.append((c, 64 * 100 * i, 64 * (4 + 3 * (i % 5)), (5e-4, 1e-3, 2e-3)[i % 3], 7 + i, chi))
+    srv = q.Server(hbm_budget_bytes=4 << 30, n_streams=16)
+    try:
+        ids = [srv.submit(c, s0, n, p=p, seed=sd, chi_max=ch, cutoff=1e-10) for c, s0, n, p, sd, ch in jobs]
+        res = _wait(srv, ids)
+    finally:
+        srv.close()
+    for (c, s0, n, p, sd, ch), j in zip(jobs, ids):
+        r = res[j]
+        assert r["state"] == 0, (r["state"], r["error"])
+        d, k = _job(q, c, s0, n, p, sd, ch)
+        assert np.array_equal(d, r["counts"]) and k == r["survivors"]
+
+
+def test_large_job_is_not_starved_by_a_stream_of_small_jobs():
+    """Shortest-remaining-work first, aged: a large job that shares two worker streams with a steady
+    stream of small jobs still finishes while the small jobs keep arriving."""
+    q = lib_ready()
+    c17 = q.Circuit(workload_circuit("d3_17q_12l", layers=3))
+    c_big = q.Circuit(workload_circuit("d3_17q_12l"))
+    big = (c_big, 0, 64 * 60, 2e-3, 1, 32)
+    srv = q.Server(hbm_budget_bytes=8 << 30, n_streams=2)
+    try:
+        t0 = time.time()
+        jb = srv.submit(big[0], *big[1:3], p=big[3], seed=big[4], chi_max=big[5], cutoff=1e-10)
+        alone_s = None
+        while srv.poll(jb) is None:
+            time.sleep(0.002)
+        alone_s = time.time() - t0
+    finally:
+        srv.close()
+    window = max(4.0, 4 * alone_s + 3.0)
+    srv = q.Server(hbm_budget_bytes=8 << 30, n_streams=2)
+    try:
+        small, k = [], 0
+        t0 = time.time()
+        jb = srv.submit(big[0], 64 * 5000, big[2], p=big[3], seed=big[4], chi_max=big[5], cutoff=1e-10)
+        big_done = None
+        while time.time() - t0 < window:
+            small.append(srv.submit(c17, 64 * 10 * k, 64 * 2, p=1e-3, seed=k, chi_max=32, cutoff=1e-10))
+            k += 1
+            if big_done is None and srv.poll(jb) is not None:
+                big_done = time.time() - t0
+            time.sleep(0.01)
+        _wait(srv, small + [jb])
+        r = srv.poll(jb)
+    finally:
+        srv.close()
+    assert r["state"] == 0, r["error"]
+    assert big_done is not None and big_done < window, (big_done, window, alone_s)

@@ -116,3 +116,29 @@ def test_readout_uniform():
     assert abs(u.mean() - 0.5) < 5 * math.sqrt(1 / 12 / len(u))
     # 53-bit resolution: values are multiples of 2^-53
     assert all((x * 2**53) == int(x * 2**53) for x in u[:100])
+
+
+@pytest.mark.parametrize("p", [1e-3, 0.05, 0.3])
+def test_vectorised_fault_sampler_equals_scalar_contract(p):
+    """The vectorised Bernoulli sampler (every test's fault source) against the scalar statement of
+    the contract: for every channel and every word, the lanes of `faulted_lanes` (first lane from the
+    word draw, then geometric skips while the next lane stays below 64) and the Pauli of each lane
+    from `pauli_code`.  At p = 0.3 a word holds ~19 faulted lanes, so the skip counter passes several
+    Philox blocks (k >> 2 > 0) and the walk stops at the word's end; at p = 1e-3 most words have none."""
+    from oracle.philox import faulted_lanes, pauli_code, sample_faults_bernoulli, thresholds
+    kinds = ["DEP1", "DEP2", "XERR", "DEP2", "DEP1", "XERR", "DEP2"] * 3
+    seed = 0x1234_5678_9ABC
+    shots = list(range(0, 3 * 64)) + [64 * 1000 + 5, 64 * 77777 + 63]
+    got = sample_faults_bernoulli(seed, kinds, p, shots)
+    _, tg = thresholds(p)
+    expect = {s: [] for s in shots}
+    for w in sorted({s >> 6 for s in shots}):
+        for c, kind in enumerate(kinds):
+            for lane in faulted_lanes(seed, c, w, tg):
+                s = (w << 6) | lane
+                if s in expect:
+                    expect[s].append((c, pauli_code(seed, c, w, lane, kind)))
+    for s in shots:
+        assert got[s] == sorted(expect[s]), s
+    if p >= 0.05:
+        assert max(len(v) for v in got.values()) >= 3
