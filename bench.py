@@ -43,12 +43,14 @@ def parse_args():
     ap.add_argument("--survivors", type=int, default=8192, help="target pre-screen survivors per step")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-sample-shots", type=int, default=1)
+    ap.add_argument("--cpu-procs", type=int, default=0, help="oracle processes (0 = the host cores available)")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-comparator", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=5.0)
-    ap.add_argument("--subsets", action="store_true",
-                    help="also run the subset-sampling leg: exactly k faults, k = 0..4, chi_max 1024")
+    ap.add_argument("--no-subsets", action="store_true",
+                    help="skip the subset-sampling leg (exactly k faults, k = 0..4, chi_max 1024)")
+    ap.add_argument("--no-legs", action="store_true",
+                    help="skip the other configurations (17-qubit complex128, 1e8-shot pre-screen, chi_max rows)")
     ap.add_argument("--case", default=None, choices=["engine-prefix6", "prescreen-1e7"],
                     help="run one small profiling case once and print its timing (for ncu captures)")
     return ap.parse_args()
@@ -128,62 +130,141 @@ def engine_traffic():
     return ENGINE_TRAFFIC["bytes_per_launch"] if digest == ENGINE_TRAFFIC["mps_cu_sha256"] else None
 
 
-def fp32_alu_peak_tflops(sm_max_mhz):
-    """FP32 FMA issue peak: 148 SMs x 128 FP32 lanes x 2 flops x SM clock."""
-    return 148 * 128 * 2 * sm_max_mhz * 1e6 / 1e12
+def fp32_alu_peak_tflops(sm_max_mhz, nsm=148):
+    """Fallback FP32 FMA issue peak from unit counts: SMs x 128 FP32 lanes x 2 flops x SM clock."""
+    return nsm * 128 * 2 * sm_max_mhz * 1e6 / 1e12
 
 
-# ---- CPU oracle baseline ----------------------------------------------------------------------
-def cpu_oracle_rate(text, shots, args):
-    """The oracle (FP64 NumPy MPS) as it stands, one process, on the given survivor shots."""
-    os.environ.setdefault("OMP_NUM_THREADS", "1")
-    from oracle import sampler
+def alu_peaks(q):
+    """Measured issue rates of this device (qc_measure_alu_peaks), or None when the call fails."""
+    try:
+        return q.measure_alu_peaks()
+    except Exception as e:  # noqa: BLE001 - reported in the JSON line
+        return {"error": str(e)}
+
+
+def prescreen_int_ops_per_word(text, decided):
+    """Algorithmic 32-bit integer operations of the pre-screen per 64-shot word (Sec. 4.2):
+    frame updates as 64-bit logic on x/z words (S: z ^= x; CX, CZ: two XORs; a decided M: one OR
+    into the rejection word; H, SWAP and clears move words and count nothing), each 64-bit operation
+    two 32-bit ones; noise: one Philox4x32-10 block (10 rounds of two 32x32 multiplies with high and
+    low halves, four XORs, two key additions: 100 operations) per four channels plus the threshold
+    compare.  The rare lane walks of faulted (channel, word) pairs are not counted."""
+    ops, mi = 0, 0
+    for line in text.splitlines():
+        t = line.split("#", 1)[0].split()
+        if not t:
+            continue
+        k = t[0]
+        if k in ("S", "SDG"):
+            ops += 2
+        elif k in ("CX", "CZ"):
+            ops += 4
+        elif k in ("DEP1", "DEP2", "XERR"):
+            ops += 26
+        elif k == "M":
+            ops += 2 if decided[mi] else 0
+            mi += 1
+    return ops
+
+
+# ---- CPU oracle baseline: one spawn-started process per host core -------------------------------
+_ORC = {}
+
+
+def _oracle_init(text):
     from oracle.circuit import parse
-    oc = parse(text)
+    _ORC["circ"] = parse(text)
+
+
+def _oracle_task(task):
+    """One survivor shot through the oracle's FP64 NumPy MPS pipeline, as it stands."""
+    shot, p, seed, chi_max, cutoff = task
+    from oracle import sampler
     t0 = time.perf_counter()
-    counts, res = sampler.sample(oc, p=args.p, seed=args.seed, shots=shots, engine="mps",
-                                 chi_max=args.chi_max, cutoff=args.cutoff, prescreen=False)
-    dt = time.perf_counter() - t0
-    acc = sum(1 for r in res if r.accepted)
-    return acc, len(shots), dt
+    _, res = sampler.sample(_ORC["circ"], p=p, seed=seed, shots=[shot], engine="mps", chi_max=chi_max,
+                            cutoff=cutoff, prescreen=False)
+    return int(sum(1 for r in res if r.accepted)), time.perf_counter() - t0
 
 
-def run_reference(args):
-    """The reference arm: the CPU oracle timed on the same workload, a bounded sample per step."""
-    rank = int(os.environ.get("RANK", "0"))
-    if rank != 0:
-        return
-    from synth import workload_circuit
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+class OraclePool:
+    """The oracle timed on the host cores: a spawn-started pool (one BLAS thread per process), warmed
+    up before timing so that interpreter and NumPy start-up are not counted."""
+
+    def __init__(self, text, procs):
+        import multiprocessing as mp
+        os.environ["OMP_NUM_THREADS"] = "1"
+        os.environ["OPENBLAS_NUM_THREADS"] = "1"
+        self.procs = procs
+        self.pool = mp.get_context("spawn").Pool(procs, initializer=_oracle_init, initargs=(text,))
+        self.pool.map(_oracle_init, [text] * procs)
+
+    def run(self, shots, args):
+        t0 = time.perf_counter()
+        out = self.pool.map(_oracle_task, [(int(s), args.p, args.seed, args.chi_max, args.cutoff) for s in shots],
+                            chunksize=1)
+        wall = time.perf_counter() - t0
+        return sum(a for a, _ in out), len(shots), wall, sum(t for _, t in out)
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def oracle_survivors(text, count, args):
+    """Survivor shots of the workload found by the oracle's own pre-screen (the first drawn blocks)."""
     from oracle import prescreen, sampler
     from oracle.circuit import parse
-    text = workload_circuit(WORKLOAD, seed=args.seed)
     oc = parse(text)
     dec = prescreen.decided_measurements(oc)
-    # survivors of the first drawn block, found by the oracle's own pre-screen
-    surv = []
-    block = 0
-    while len(surv) < args.steps + args.warmup and block < 64:
+    surv, block = [], 0
+    while len(surv) < count and block < 256:
         shots = range(block * 64 * 512, (block + 1) * 64 * 512)
         f = sampler.draw_faults(oc, p=args.p, seed=args.seed, shots=shots)
         kept = prescreen.frame_prescreen(oc, dec, f)
         surv += [s for s in shots if kept[s]]
         block += 1
-    times, accs = [], []
-    for k in range(args.warmup + args.steps):
-        acc, n, dt = cpu_oracle_rate(text, [surv[k % len(surv)]], args)
-        if k >= args.warmup:
-            times.append(dt)
-            accs.append(acc)
-    tot = sum(times)
-    value = sum(accs) / tot if tot > 0 else 0.0
+    return surv[:count]
+
+
+def run_reference(args):
+    """The reference arm: the CPU oracle timed on the host cores on the same workload, each step a
+    bounded sample (one pre-screen survivor per process)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from synth import workload_circuit
+    text = workload_circuit(WORKLOAD, seed=args.seed)
+    procs = args.cpu_procs or host_cores()
+    surv = oracle_survivors(text, procs * (args.steps + 1), args)
+    pool = OraclePool(text, procs)
+    try:
+        for _ in range(args.warmup):  # warm-up steps: one short shot per process
+            pool.pool.map(_oracle_init, [text] * procs)
+        acc, n, wall = 0, 0, 0.0
+        for k in range(args.steps):
+            a, m, w, _ = pool.run(surv[k * procs:(k + 1) * procs], args)
+            acc, n, wall = acc + a, n + m, wall + w
+    finally:
+        pool.close()
+    value = acc / wall if wall > 0 else 0.0
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "shots/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / max(1, args.steps),
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / max(1, args.steps),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": f"{WORKLOAD}: 49 qubits (25 data + 24 ancilla), 60 layers, 16 T, p={args.p}",
-                       "chi_max": args.chi_max, "cutoff": args.cutoff, "shots_per_step": 1},
-            "cpu_baseline": {"value": value, "unit": "shots/s", "cores": 1, "kind": "oracle",
-                             "sample": "one pre-screen survivor per step through the FP64 NumPy MPS oracle"},
+                       "chi_max": args.chi_max, "cutoff": args.cutoff, "shots_per_step": procs},
+            "cpu_baseline": {"value": value, "unit": "shots/s", "cores": procs, "kind": "oracle",
+                             "sample": f"{procs} pre-screen survivors per step, one per process, through the "
+                                       f"FP64 NumPy MPS oracle ({procs} spawn-started processes, one BLAS "
+                                       f"thread each)"},
             "e2e": {"value": value, "unit": "shots/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -326,6 +407,83 @@ def subsets_leg(q, np, circ, args, target=1024, chi=1024):
     return {"chi_max": chi, "target_survivors_per_k": target, "per_k": out}
 
 
+# ---- the other configurations -------------------------------------------------------------------
+def _timed(fn):
+    """Device time of fn() in seconds (CUDA events on the current stream) and its result."""
+    import torch
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(st)
+    out = fn()
+    e1.record(st)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1e3, out
+
+
+def c1_leg(q, args):
+    """17 qubits (9 data + 8 ancilla), 12 layers, 4 T per layer, p = 1e-3, chi_max 32, cutoff 1e-12,
+    complex128, 1,000 drawn shots: pre-screen + engine, device-timed (a fresh shot range, after one
+    warm-up run that builds the reference state)."""
+    from synth import workload_circuit
+    c = q.Circuit(workload_circuit("d3_17q_12l", seed=args.seed))
+
+    def run(shot0):
+        pre = q.pauli_prescreen(c, shot0, 1000, p=1e-3, seed=args.seed)
+        counts, res = q.mps_sample_batch(c, pre["survivors"], p=1e-3, seed=args.seed, chi_max=32, cutoff=1e-12,
+                                         precision=q.QC_C128, per_shot=True, copy_back=False)
+        return pre, counts
+
+    run(0)
+    dt, (pre, counts) = _timed(lambda: run(64 * 1_000_000))
+    acc = int(counts[:, 1].sum())
+    return {"workload": "d3_17q_12l: 17 qubits, 12 layers, 4 T/layer, p=1e-3", "chi_max": 32, "cutoff": 1e-12,
+            "dtype": "c128", "drawn": 1000, "survivors": int(pre["n_kept"]), "accepted": acc,
+            "logical_errors": int(counts[:, 2].sum()), "seconds": dt,
+            "accepted_shots_per_s": acc / dt if dt > 0 else None}
+
+
+def c2_leg(q, args, peaks):
+    """The pre-screen alone: 1e8 shots of the 49-qubit, 200-layer circuit (16 T, p = 1e-3) as bit-packed
+    64-shot frames (kept mask and per-weight histograms, no survivor list), device-timed; its integer
+    roofline against the measured 32-bit logic rate."""
+    from synth import workload_circuit
+    text = workload_circuit("d5_49q_200l", seed=args.seed)
+    c = q.Circuit(text)
+    n = 10 ** 8
+    q.pauli_prescreen(c, 0, 64 * 4096, p=1e-3, seed=args.seed, survivors_capacity=0)
+    dt, out = _timed(lambda: q.pauli_prescreen(c, 64 * 10_000_000, n, p=1e-3, seed=args.seed, survivors_capacity=0))
+    ops_word = prescreen_int_ops_per_word(text, list(c.decided()))
+    words = (n + 63) // 64
+    achieved = ops_word * words / dt / 1e12 if dt > 0 else 0.0
+    peak = peaks.get("lop3_tops") if isinstance(peaks, dict) else None
+    return {"workload": "d5_49q_200l: 49 qubits, 200 layers, 16 T, p=1e-3", "shots": n, "seconds": dt,
+            "shots_per_s": n / dt if dt > 0 else None, "kept": int(out["n_kept"]),
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s (32-bit integer)",
+                         "frac": achieved / peak if peak else None, "ops_per_word": ops_word,
+                         "peak_note": "measured 32-bit three-input logic rate (qc_measure_alu_peaks)",
+                         "ops_note": "model: frame logic + one Philox4x32-10 block per four channels per 64-shot "
+                                     "word; lane walks of faulted words not counted"}}
+
+
+def chi_rows_leg(q, circ, args, chis=(64, 128), survivors=2048):
+    """Config 3 at the other chi_max values: one device-timed batch of `survivors` pre-screen survivors
+    of the 49-qubit workload per chi_max (complex64, cutoff 1e-10)."""
+    out = {}
+    pre = q.pauli_prescreen(circ, 64 * 50_000_000, int(math.ceil(survivors / 0.00125 / 64.0)) * 64 * 2,
+                            p=args.p, seed=args.seed)
+    surv = pre["survivors"][:survivors]
+    for chi in chis:
+        q.mps_sample_batch(circ, surv[:1], p=args.p, seed=args.seed, chi_max=chi, cutoff=args.cutoff, per_shot=False)
+        dt, (counts, res) = _timed(lambda: q.mps_sample_batch(circ, surv, p=args.p, seed=args.seed, chi_max=chi,
+                                                              cutoff=args.cutoff, per_shot=True))
+        acc = int(counts[:, 1].sum())
+        out[str(chi)] = {"survivors": int(surv.numel()), "accepted": acc, "seconds": dt,
+                         "accepted_shots_per_s": acc / dt if dt > 0 else None,
+                         "chi_peak": int(res["chi_peak"].max()), "max_discarded": float(res["discarded"].max())}
+    return out
+
+
 # ---- the GPU arm ------------------------------------------------------------------------------
 def profiling_case(args):
     """Small, self-contained cases for ncu: the MPS engine on the 6-layer prefix of the 49-qubit
@@ -387,6 +545,7 @@ def main():
     text = workload_circuit(WORKLOAD, seed=args.seed)
     circ = q.Circuit(text)
     info = circ.info()
+    peaks = alu_peaks(q)
     keep_rate = 0.00125  # pre-screen keep rate of this workload at p = 1e-3 (measured)
     drawn = max(64, int(math.ceil(args.survivors / keep_rate / 64.0)) * 64)
     stream = torch.cuda.current_stream()
@@ -399,7 +558,7 @@ def main():
         return rank_shot0(rank, step, drawn)
 
     kernel_ms = []
-    flops_acc = [0.0]
+    flops_dev = torch.zeros((), dtype=torch.float64, device="cuda")  # summed over the timed steps
     last = {}
 
     def step(k, timed):
@@ -414,6 +573,10 @@ def main():
         e1.record(stream)
         if timed:
             kernel_ms.append((e0, e1, int(surv.numel())))
+            # algorithmic flops of this step's shots, summed on the device (alg_flops of each record)
+            recs = shot_buf[: surv.numel() * q.SHOT_DTYPE.itemsize].view(torch.float64)
+            recs = recs.view(-1, q.SHOT_DTYPE.itemsize // 8)
+            flops_dev.add_(recs[:, q.SHOT_DTYPE.fields["alg_flops"][1] // 8].sum())
         last["counts"] = counts
         last["n"] = int(surv.numel())
         return int(counts[:, 1].sum()), int(surv.numel())
@@ -448,14 +611,17 @@ def main():
     # roofline of the dominant kernel (the MPS engine): algorithmic flops / event time
     eng_ms = sum(a.elapsed_time(b) for a, b, _ in kernel_ms)
     res = shot_results(shot_buf, last["n"])
-    flops_last = float(res["alg_flops"].sum())
-    # flops of every timed step: re-derive from the per-step survivor counts with the last step's
-    # mean (steps are statistically identical); the last step's exact figure is reported too
     n_timed = sum(n for _, _, n in kernel_ms)
-    flops_timed = flops_last / max(1, last["n"]) * n_timed
-    peaks = measured_peaks()
-    smax = peaks.get("sm_max_mhz", 2032.0)
-    alu_peak = fp32_alu_peak_tflops(smax)
+    flops_timed = float(flops_dev)
+    if isinstance(peaks, dict) and peaks.get("ffma_tflops"):
+        alu_peak = max(peaks["ffma_tflops"], peaks["ffma2_tflops"])
+        peak_note = ("measured FP32 FMA issue rate on this device: max(FFMA %.1f, paired FFMA2 %.1f) TFLOP/s "
+                     "(qc_measure_alu_peaks; %d SMs)" % (peaks["ffma_tflops"], peaks["ffma2_tflops"],
+                                                        peaks["sm_count"]))
+    else:
+        smax = measured_peaks().get("sm_max_mhz", 2032.0)
+        alu_peak = fp32_alu_peak_tflops(smax)
+        peak_note = "fallback (measurement failed): 148 SM x 128 FP32 lanes x 2 x %.0f MHz" % smax
     achieved = flops_timed / (eng_ms / 1e3) / 1e12 if eng_ms > 0 else 0.0
 
     # end-to-end leg through the C ABI with host buffers: the survivor list goes to the host and
@@ -493,7 +659,11 @@ def main():
     if not args.no_serving and world == 1:
         circ17 = q.Circuit(workload_circuit("d3_17q_12l", seed=args.seed))
         serving = serving_leg(q, np, circ17, circ, duration_s=args.serve_seconds)
-    subsets = subsets_leg(q, np, circ, args) if args.subsets else None
+    subsets = subsets_leg(q, np, circ, args) if not args.no_subsets else None
+    legs = None
+    if not args.no_legs:
+        legs = {"c1_17q_c128": c1_leg(q, args), "c2_prescreen_1e8": c2_leg(q, args, peaks),
+                "c3_chi_rows": chi_rows_leg(q, circ, args)}
     comparator = None
     if not args.no_comparator:
         comparator = comparator_leg(q, text, circ, int(res["shot"][0]), args)
@@ -501,11 +671,17 @@ def main():
 
     cpu = None
     if not args.no_cpu_baseline:
-        picks = [int(s) for s in res["shot"][: args.cpu_sample_shots]]
-        acc, n, dt = cpu_oracle_rate(text, picks, args)
-        cpu = {"value": (acc / dt) if dt > 0 else 0.0, "unit": "shots/s", "cores": 1, "kind": "oracle",
-               "sample": f"{n} pre-screen survivor shot(s) of this workload through the FP64 NumPy MPS "
-                         f"oracle, one process ({dt:.1f} s)"}
+        procs = args.cpu_procs or host_cores()
+        picks = [int(s) for s in res["shot"][:procs]]
+        pool = OraclePool(text, procs)
+        try:
+            acc, n, wall, busy = pool.run(picks, args)
+        finally:
+            pool.close()
+        cpu = {"value": (acc / wall) if wall > 0 else 0.0, "unit": "shots/s", "cores": procs, "kind": "oracle",
+               "sample": f"{n} pre-screen survivor shots of this workload (the first of the last timed step), "
+                         f"one per process, through the FP64 NumPy MPS oracle on {procs} spawn-started "
+                         f"processes with one BLAS thread each: {wall:.1f} s wall, {busy:.1f} s summed"}
 
     line = {
         "metric": METRIC, "value": value, "unit": "shots/s", "n_gpus": world, "steps": args.steps,
@@ -523,10 +699,10 @@ def main():
                      "traffic_note": "DRAM read+write bytes per engine launch from one ncu capture of this "
                                      "engine source (null when the source changed since)",
                      "kernel": "engine_kernel<float,32> (one warp per shot)",
-                     "peak_note": "FP32 FMA issue rate 148 SM x 128 lanes x 2 x %.0f MHz (%s)" % (
-                         smax, "sm_max_mhz of MEASURED_PEAKS.json" if "sm_max_mhz" in peaks
-                         else "fallback: the B300's maximum SM clock, MEASURED_PEAKS.json absent"),
-                     "alg_flops_per_shot": flops_last / max(1, last["n"]), "engine_ms": eng_ms},
+                     "peak_note": peak_note,
+                     "flops_note": "algorithmic flops counted per shot by the engine and summed on the device "
+                                   "over every timed step",
+                     "alg_flops_per_shot": flops_timed / max(1, n_timed), "engine_ms": eng_ms},
         "clocks": clocks,
         "e2e": {"value": e2e_val, "unit": "shots/s", "h2d_bytes_per_step": h2d // e2e_steps,
                 "d2h_bytes_per_step": d2h // e2e_steps},
@@ -534,6 +710,8 @@ def main():
         "serving": serving,
         "plain_fp64_gpu": comparator,
         "subsets": subsets,
+        "legs": legs,
+        "alu_peaks": peaks,
         "wall_s": wall,
     }
     print(json.dumps(line), flush=True)

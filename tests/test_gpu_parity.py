@@ -4,8 +4,8 @@
   shots than SMs, complex64, chi_max 256, cutoff 1e-10): there every 64-wide theta is rotated in
   global memory by the blocked Jacobi.  Fidelity and every readout probability at 1e-4 absolute
   (the complex64 tolerance), on shots sampled across the batch.
-* The blocked Jacobi forced at complex128 (a small shared-memory work area) on the 17-qubit
-  workload: fidelity and readout probabilities at 1e-10.
+* The blocked Jacobi forced at complex128 (a small shared-memory work area) on the 49-qubit
+  workload's 6-layer prefix: fidelity and readout probabilities at 1e-10.
 * Per-readout Born probabilities of the default (one CTA per shot) complex128 engine at 1e-10.
 * Logical-error and acceptance rates of the 17-qubit, 1,000-shot configuration against the
   oracle's own pre-screen + MPS pipeline, within binomial intervals.
@@ -81,23 +81,24 @@ def test_benchmark_launch_warp_engine_blocked_jacobi_c64():
 
 
 def test_blocked_jacobi_forced_c128(monkeypatch):
-    """An 8 KB work area per warp sends every theta wider than ~8 columns to global memory, so the
-    blocked Jacobi (blocks of 4 columns) runs on most splits of the 17-qubit workload."""
+    """A 12 KB work area per warp at complex128 on a 6-layer prefix of the 49-qubit workload: every
+    64-wide theta goes to global memory and is rotated by the blocked Jacobi in blocks of 3 columns
+    (12 KB holds ~430 complex128 elements next to the fixed arrays, 2 blocks x 65 rows each fit)."""
     monkeypatch.setenv("QCMPS_ENGINE", "warp")
-    monkeypatch.setenv("QCMPS_SMEM_KB", "8")
+    monkeypatch.setenv("QCMPS_SMEM_KB", "12")
     q = lib_ready()
-    text = workload_circuit("d3_17q_12l")
+    text = workload_circuit("d5_49q_60l", layers=6)
     c = q.Circuit(text)
-    p, seed = 4e-3, 13
-    shots = q.pauli_prescreen(c, 0, 64 * 8, p=p, seed=seed)["survivors"][:32]
+    p, seed = 2e-3, 13
+    shots = q.pauli_prescreen(c, 0, 64 * 64, p=p, seed=seed)["survivors"][:16]
     K = _n_readouts(c)
-    _, res, rec = q.mps_sample_batch_traced(c, shots, p=p, seed=seed, chi_max=32, cutoff=1e-12,
+    _, res, rec = q.mps_sample_batch_traced(c, shots, p=p, seed=seed, chi_max=256, cutoff=1e-12,
                                             precision=q.QC_C128, readout_k=K)
     pick = [int(s) for s in res["shot"]]
     faults = sampler.draw_faults(parse(text), p=p, seed=seed, shots=pick)
-    ref = oracle_shots(text, pick, faults, seed=seed, chi_max=32, cutoff=1e-12)
+    ref = oracle_shots(text, pick, faults, seed=seed, chi_max=256, cutoff=1e-12)
     _compare(res, rec, ref, 1e-10, 1e-10)
-    assert (res[res["status"] == 0]["gmem_updates"] > 0).all()
+    assert (res["gmem_updates"] > 0).all(), res["gmem_updates"]
 
 
 @pytest.mark.parametrize("prec,tol", [(1, 1e-10), (0, 1e-4)])
