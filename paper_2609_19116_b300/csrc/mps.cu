@@ -297,25 +297,65 @@ struct Engine {
         }
     }
 
-    // ---- one-sided Jacobi on the columns of X (rows x cols, leading dimension ld) ---------------
-    // Round-robin ordering: n-1 rounds of n/2 disjoint column pairs.  The pairs of a round are
-    // spread over the warps, and within a warp over lane groups of g lanes (g = 32 / pairs per warp,
-    // rounded), so that small matrices keep every lane busy and reduce over short shuffle trees.
-    // Pairs whose smaller column is below the numerical floor are left alone: such a column is
-    // rounding noise of a rank-deficient theta, and rotating it against a large column never
-    // reaches relative orthogonality.
+    // ---- one Jacobi rotation of a column pair ------------------------------------------------------
+    // The g lanes of a group (gl = lane within the group) form alpha = |a|^2, beta = |b|^2 and
+    // gamma = a^H b over the rows and, unless the pair is already orthogonal to the tolerance, rotate
+    // it.  Every lane takes part in the shuffles; `act` marks groups that own a pair.  Pairs whose
+    // smaller column is below the numerical floor are left alone: such a column is rounding noise of
+    // a rank-deficient theta, and rotating it against a large column never reaches relative
+    // orthogonality.  Returns 1 when this lane's group rotated.
+    __device__ __forceinline__ int pair_step(V* a, V* b, int rows, int gl, int g, bool act, R tol, R floor2) {
+        R al = 0, be = 0, gr = 0, gi = 0;
+        if (act) pair_dots(a, b, rows, gl, g, al, be, gr, gi);
+        for (int o = g >> 1; o > 0; o >>= 1) {
+            al += __shfl_xor_sync(0xFFFFFFFFu, al, o);
+            be += __shfl_xor_sync(0xFFFFFFFFu, be, o);
+            gr += __shfl_xor_sync(0xFFFFFFFFu, gr, o);
+            gi += __shfl_xor_sync(0xFFFFFFFFu, gi, o);
+        }
+        const R g2 = gr * gr + gi * gi;
+        if (act && g2 > tol * tol * (al * be) && g2 > (R)0 && fmin(al, be) > floor2) {
+            const R rg = rs_sqrt(g2);                    // 1 / |gamma|
+            const R zeta = (be - al) * (R)0.5 * rg;
+            const R t = fdiv(zeta >= 0 ? (R)1 : (R)-1, fabs(zeta) + sqrt((R)1 + zeta * zeta));
+            const R c = rs_sqrt((R)1 + t * t), sn = c * t;
+            pair_rotate(a, b, rows, gl, g, c, sn * gr * rg, -sn * gi * rg);
+            return 1;
+        }
+        return 0;
+    }
+
+    // Lane groups for `pairs` concurrent pairs: G groups of g = 32 / G lanes per warp (G a power of
+    // two, at least 2 lanes per pair when the rows allow it), so that small matrices keep every lane
+    // busy and reduce over short shuffle trees.
+    __device__ __forceinline__ void lane_groups(int pairs, int rows, int& G, int& g, int& grp, int& gl) const {
+        constexpr int NW = NT / 32;
+        const int lane = tid_ & 31;
+        const int ppw = (pairs + NW - 1) / NW;
+        G = 1;
+        while (G < ppw && G < 32) G <<= 1;
+        while (G > 1 && 32 / G < 2 && rows > 32 / G) G >>= 1;
+        g = 32 / G;
+        grp = lane / g;
+        gl = lane - grp * g;
+    }
+
+    __device__ __forceinline__ R jacobi_tol(int rows) const {
+        const R eps = sizeof(R) == 4 ? (R)FLT_EPSILON : (R)DBL_EPSILON;
+        return (R)4 * eps * sqrt((R)rows);
+    }
+
+    // ---- one-sided Jacobi on the columns of X (rows x cols, cols even, leading dimension ld) -----
+    // Round-robin ordering: cols-1 rounds of cols/2 disjoint column pairs, spread over the warps and
+    // their lane groups.
     __device__ bool jacobi(V* X, int rows, int cols, int ld, R floor2, int max_sweeps = 0,
                            int* any_rotation = nullptr) {
-        const int lane = tid_ & 31, wid = tid_ >> 5;
+        const int wid = tid_ >> 5;
         constexpr int NW = NT / 32;
-        const R eps = sizeof(R) == 4 ? (R)FLT_EPSILON : (R)DBL_EPSILON;
-        const R tol = (R)4 * eps * sqrt((R)rows);
+        const R tol = jacobi_tol(rows);
         const int half = cols / 2, cm1 = cols - 1;
-        const int ppw = (half + NW - 1) / NW;
-        int G = 1;
-        while (G < ppw && G < 32) G <<= 1;
-        while (G > 1 && 32 / G < 2 && rows > 32 / G) G >>= 1;  // keep at least 2 lanes per pair when useful
-        const int g = 32 / G, grp = lane / g, gl = lane - grp * g;
+        int G, g, grp, gl;
+        lane_groups(half, rows, G, g, grp, gl);
         const int cap = max_sweeps > 0 ? max_sweeps : P.sweep_cap;
         for (int sweep = 0; sweep < cap; ++sweep) {
             int rotated = 0;
@@ -330,25 +370,7 @@ struct Engine {
                     ib -= ib >= cm1 ? cm1 : 0;
                     const int ca = sa == 0 ? 0 : 1 + ia;
                     const int cb = 1 + ib;
-                    V* a = X + (size_t)ca * ld;
-                    V* b = X + (size_t)cb * ld;
-                    R al = 0, be = 0, gr = 0, gi = 0;
-                    if (act) pair_dots(a, b, rows, gl, g, al, be, gr, gi);
-                    for (int o = g >> 1; o > 0; o >>= 1) {
-                        al += __shfl_xor_sync(0xFFFFFFFFu, al, o);
-                        be += __shfl_xor_sync(0xFFFFFFFFu, be, o);
-                        gr += __shfl_xor_sync(0xFFFFFFFFu, gr, o);
-                        gi += __shfl_xor_sync(0xFFFFFFFFu, gi, o);
-                    }
-                    const R g2 = gr * gr + gi * gi;
-                    if (act && g2 > tol * tol * (al * be) && g2 > (R)0 && fmin(al, be) > floor2) {
-                        rotated = 1;
-                        const R rg = rs_sqrt(g2);                    // 1 / |gamma|
-                        const R zeta = (be - al) * (R)0.5 * rg;
-                        const R t = fdiv(zeta >= 0 ? (R)1 : (R)-1, fabs(zeta) + sqrt((R)1 + zeta * zeta));
-                        const R c = rs_sqrt((R)1 + t * t), sn = c * t;
-                        pair_rotate(a, b, rows, gl, g, c, sn * gr * rg, -sn * gi * rg);
-                    }
+                    rotated |= pair_step(X + (size_t)ca * ld, X + (size_t)cb * ld, rows, gl, g, act, tol, floor2);
                 }
                 bsync<NT>();
             }
@@ -360,11 +382,41 @@ struct Engine {
         return max_sweeps > 0;  // an inner pass is not required to converge on its own
     }
 
+    // ---- the cross pairs of two column blocks held side by side in X ------------------------------
+    // Columns [0, ni) and [ni, ni + nj).  Round k pairs column i of the smaller block with column
+    // (i + k) mod n_l of the larger (n_l columns): each round is a set of disjoint pairs, and n_l
+    // rounds visit all ni x nj pairs once.  Returns 1 when this thread's group rotated.
+    __device__ int cross_pass(V* X, int rows, int ni, int nj, int ld, R floor2) {
+        const int wid = tid_ >> 5;
+        constexpr int NW = NT / 32;
+        const R tol = jacobi_tol(rows);
+        const bool sw = ni > nj;
+        const int ns = sw ? nj : ni, nl = sw ? ni : nj;
+        const int s0 = sw ? ni : 0, l0 = sw ? 0 : ni;
+        int G, g, grp, gl;
+        lane_groups(ns, rows, G, g, grp, gl);
+        int rotated = 0;
+        for (int k = 0; k < nl; ++k) {
+            for (int base = wid * G; base < ns; base += NW * G) {
+                const int i = base + grp;
+                const bool act = i < ns;
+                const int ii = act ? i : 0;
+                int j = ii + k;
+                j -= j >= nl ? nl : 0;
+                rotated |= pair_step(X + (size_t)(s0 + ii) * ld, X + (size_t)(l0 + j) * ld, rows, gl, g, act, tol,
+                                     floor2);
+            }
+            bsync<NT>();
+        }
+        return rotated;
+    }
+
     // ---- block Jacobi for an X that lives in global memory ----------------------------------------
-    // The columns are cut into blocks of bw that fit twice into the shared work area; blocks are
-    // paired round-robin, each pair is copied into shared memory once per outer round, all column
-    // pairs inside it are rotated there (a few inner sweeps), and the pair is written back.  Global
-    // traffic per outer sweep drops by about bw against rotating column pairs in place.
+    // The columns are cut into blocks of bw (even) that fit twice into the shared work area W.  One
+    // outer sweep visits every column pair exactly once, as one cyclic sweep of the plain Jacobi does
+    // in another order: the blocks are paired round-robin; each pair is staged into shared memory once,
+    // in the first round each block's internal pairs get one round-robin pass, and in every round the
+    // staged pair's cross pairs are rotated; then the pair is written back.
     __device__ bool jacobi_blocked(V* X, int rows, int cols, int ld, R floor2, V* W, int bw) {
         const int lw = rows + 1;
         const int nb = (cols + bw - 1) / bw;
@@ -379,20 +431,21 @@ struct Engine {
                     ib -= ib >= nbp - 1 ? nbp - 1 : 0;
                     const int bi = sa == 0 ? 0 : 1 + ia;
                     const int bj = 1 + ib;
-                    const int i0 = bi * bw, i1 = min(cols, i0 + bw);
-                    const int j0 = bj * bw, j1 = min(cols, j0 + bw);
-                    const int ni = bi < nb ? i1 - i0 : 0, nj = bj < nb ? j1 - j0 : 0;
-                    if (ni + nj < 2) continue;
-                    const int nc = ni + nj, ncp = nc + (nc & 1);
-                    for (int e = tid_; e < ncp * rows; e += NT) {
+                    const int i0 = bi * bw, j0 = bj * bw;
+                    const int ni = bi < nb ? min(cols, i0 + bw) - i0 : 0;
+                    const int nj = bj < nb ? min(cols, j0 + bw) - j0 : 0;
+                    const int nc = ni + nj;
+                    if (nc == 0) continue;
+                    for (int e = tid_; e < nc * rows; e += NT) {
                         const int c = e / rows, i = e - c * rows;
-                        V v = cmk<V>(0, 0);
-                        if (c < ni) v = X[(size_t)(i0 + c) * ld + i];
-                        else if (c < nc) v = X[(size_t)(j0 + c - ni) * ld + i];
-                        W[(size_t)c * lw + i] = v;
+                        W[(size_t)c * lw + i] = c < ni ? X[(size_t)(i0 + c) * ld + i] : X[(size_t)(j0 + c - ni) * ld + i];
                     }
                     bsync<NT>();
-                    jacobi(W, rows, ncp, lw, floor2, 3, &rot);
+                    if (k == 0) {  // every block is staged once in the first round: its internal pairs
+                        if (ni >= 2) jacobi(W, rows, ni, lw, floor2, 1, &rot);
+                        if (nj >= 2) jacobi(W + (size_t)ni * lw, rows, nj, lw, floor2, 1, &rot);
+                    }
+                    if (ni && nj) rot |= cross_pass(W, rows, ni, nj, lw, floor2);
                     for (int e = tid_; e < nc * rows; e += NT) {
                         const int c = e / rows, i = e - c * rows;
                         const V v = W[(size_t)c * lw + i];
@@ -403,7 +456,7 @@ struct Engine {
                 }
             }
             ++sweeps;
-            if (!rot) return true;
+            if (!bsync_or<NT>(rot)) return true;
         }
         return false;
     }
@@ -486,9 +539,15 @@ struct Engine {
             const double kept = warp_sum<double>(kl), dropped = warp_sum<double>(tl);
             if (lane == 0) {
                 int dg = 0;
-                if (r < cols) {  // s_{r-1} / s_r - 1 < 1e-8, compared on the squares
+                // a cut inside a cluster: the last kept and the first dropped value agree to what the
+                // working precision resolves (FP64: s_{r-1} / s_r - 1 < 1e-8, i.e. 2e-8 on the squares;
+                // FP32: the Jacobi stops at |a^H b| <= 4 eps sqrt(rows) |a||b|, so squared norms closer
+                // than 32 eps sqrt(rows) relative are not told apart); a dropped value at the numerical
+                // floor is not a cluster member
+                if (r < cols) {
                     const double a2 = (double)sig2[perm[r - 1]], b2 = (double)sig2[perm[r]];
-                    dg = b2 > 0 && a2 < b2 * (1.0 + 2e-8 + 1e-16);
+                    const double rel = sizeof(R) == 8 ? 2e-8 + 1e-16 : 32.0 * FLT_EPSILON * sqrt((double)rows);
+                    dg = b2 > (double)floor2 && a2 <= b2 * (1.0 + rel);
                 }
                 S.red[40] = tot > 0 ? dropped / tot : 0.0;
                 S.red[41] = kept > 0 ? 1.0 / sqrt(kept) : 0.0;
@@ -633,7 +692,7 @@ struct Engine {
         const R eps = sizeof(R) == 4 ? (R)FLT_EPSILON : (R)DBL_EPSILON;
         const R fl = (R)4 * eps * sqrt((R)rows);
         const R floor2 = fl * fl * (R)frod;
-        const int bw = (int)(P.x_smem / (2 * (uint32_t)(rows + 1)));
+        const int bw = (int)(P.x_smem / (2 * (uint32_t)(rows + 1))) & ~1;  // even: every block pairs up
         const bool blocked = (X == xg) && bw >= 2 && bw * 2 < cols;
         gmem_updates += (X == xg) ? 1 : 0;
         if (!(blocked ? jacobi_blocked(X, rows, cols, ld, floor2, S.X, bw) : jacobi(X, rows, cols, ld, floor2))) {
@@ -1579,7 +1638,12 @@ static qc_status run_pass(CircuitImpl& c, EngineParams<R> P, const SlotLayout& L
     // throughput mode (one warp per shot) needs many shots to fill the SMs; a batch with no more
     // shots than SMs runs in latency mode (one CTA per shot) unless the caller shares the GPU with
     // other batches (the serving loop), where throughput mode keeps more shots in flight
-    int variant = (ref.chi_peak <= 64 && (nshots > (uint64_t)nsm || P.shared_gpu)) ? 32 : NT_BIG;
+    // The warp variant only for passes whose slot capacity keeps theta at most 128 x 128: a pass at a
+    // larger capacity (the re-run of shots that outgrew the bucket) would run 256-wide or larger splits
+    // in one warp.  Such a pass takes the 128-thread CTA variant when it shares the GPU (72 KB of shared
+    // memory finds room beside other batches' warps) and the 512-thread one otherwise.
+    const bool small = P.chi_max <= 64 && ref.chi_peak <= 64;
+    int variant = (small && (nshots > (uint64_t)nsm || P.shared_gpu)) ? 32 : (P.shared_gpu ? 128 : NT_BIG);
     if (force && !strcmp(force, "warp")) variant = 32;
     if (force && !strcmp(force, "cta128")) variant = 128;
     if (force && !strcmp(force, "cta256")) variant = 256;

@@ -125,3 +125,30 @@ def test_overlap_sweep_matches_dense():
     c2 = parse(random_circuit(6, 80, seed=5, noise=False))
     _, b, _ = mps.run_shot(c2, reference=True)
     assert abs(mps.overlap(a, b) - np.vdot(a.vector(), b.vector())) < 1e-12
+
+
+def test_truncation_rule_and_degenerate_flag_on_crafted_spectra():
+    """The written truncation rule on spectra whose outcome follows from its definition: the kept count
+    is the smallest r with tail sum s_i^2 (i >= r) <= cutoff x total, capped by chi_max; the cut is
+    flagged degenerate exactly when the last kept and the first dropped value agree to 1e-8 relative."""
+    from oracle.mps import MPS
+    flat = np.full(8, 1 / np.sqrt(8))
+    m = MPS(2, chi_max=4, cutoff=0.0)
+    assert m._truncate(flat) == 4 and m.degenerate_cuts == 1          # cut inside a flat spectrum
+    assert abs(m.discarded - 0.5) < 1e-15
+    m = MPS(2, chi_max=4, cutoff=0.0)
+    gap = np.array([0.6, 0.5, 0.4, 0.3, 0.2, 0.1])
+    assert m._truncate(gap) == 4 and m.degenerate_cuts == 0           # clear gap at the cut
+    m = MPS(2, chi_max=4, cutoff=0.0)
+    near = np.array([0.5, 0.5, 0.5, 0.5 * (1 + 5e-9), 0.5, 0.1])
+    near = -np.sort(-near)
+    assert m._truncate(near) == 4 and m.degenerate_cuts == 1          # within 1e-8 relative
+    m = MPS(2, chi_max=4, cutoff=0.0)
+    apart = np.array([0.5 * (1 + 3e-8), 0.5 * (1 + 2e-8), 0.5 * (1 + 1e-8 + 1e-9), 0.5 * (1 + 1e-8 + 1e-9), 0.5, 0.1])
+    assert m._truncate(apart) == 4 and m.degenerate_cuts == 0         # 1.1e-8 apart: not flagged
+    m = MPS(2, chi_max=8, cutoff=0.1)
+    s = np.sqrt(np.array([0.5, 0.3, 0.12, 0.05, 0.03]))
+    assert m._truncate(s) == 3 and abs(m.discarded - 0.08) < 1e-12    # tail 0.08 <= 0.1, tail at 2 is 0.2
+    m = MPS(2, chi_max=8, cutoff=0.0)
+    z = np.array([1.0, 0.0, 0.0])
+    assert m._truncate(z) == 1 and m.degenerate_cuts == 0             # exact zeros: tail 0 <= 0 at r = 1
