@@ -378,33 +378,61 @@ def comparator_leg(q, text, circ, shot, args, time_cap_s=40.0):
 
 # ---- subset sampling at large bond (exactly k faults per shot, Sec. 4.1) ---------------------------
 def subsets_leg(q, np, circ, args, target=1024, chi=1024):
-    """For k = 0..4: fixed-weight pre-screen of drawn shots until `target` survivors, then the engine
-    on them at chi_max 1024 (complex64); per k the counts and accepted shots/s of the engine."""
+    """Config 5: for k = 0..4, exactly k faults per shot (channels uniform, Sec. 4.1).  A calibration
+    block estimates the fixed-weight pre-screen's keep rate; then D_k drawn shots (about `target`
+    survivors) are pre-screened and every survivor runs on the engine at chi_max 1024 (complex64).
+    n_k = D_k counts every drawn shot (pre-screen rejections are rejections), so the counts give the
+    reweighted curve p_acc(p), p_le(p) with App. D likelihood-ratio intervals at any p (the weights
+    carry no p dependence; bins above 4 are bounded by the truncation systematic)."""
     import torch
-    out = {}
+    from paper_2609_19116_b300 import stats
+    out, counts_all = {}, np.zeros((5, 3), dtype=np.int64)
     for k in range(5):
-        surv, drawn, base = [], 0, 64 * (1 << 24) * (k + 1)
-        while len(surv) < target and drawn < 64 * 200000:
-            n = 64 * 16384
-            pre = q.pauli_prescreen(circ, base + drawn, n, p=0.0, seed=args.seed, fault_weight=k)
-            surv += pre["survivors"].cpu().tolist()
-            drawn += n
-        surv = surv[:target]
-        dev = torch.tensor(surv, dtype=torch.int64, device="cuda")
-        q.mps_sample_batch(circ, dev[:1], p=0.0, seed=args.seed, chi_max=chi, cutoff=args.cutoff, fault_weight=k,
+        base = 64 * (1 << 24) * (k + 1)
+        cal = q.pauli_prescreen(circ, base, 64 * 4096, p=0.0, seed=args.seed, fault_weight=k, survivors_capacity=0)
+        rate = max(int(cal["n_kept"]), 1) / (64 * 4096)
+        drawn = min(64 * 200000, int(math.ceil(target / rate / 64.0)) * 64)
+        pre = q.pauli_prescreen(circ, base + 64 * 4096, drawn, p=0.0, seed=args.seed, fault_weight=k)
+        surv = pre["survivors"]
+        q.mps_sample_batch(circ, surv[:1], p=0.0, seed=args.seed, chi_max=chi, cutoff=args.cutoff, fault_weight=k,
                            per_shot=False)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        counts, res = q.mps_sample_batch(circ, dev, p=0.0, seed=args.seed, chi_max=chi, cutoff=args.cutoff,
-                                         fault_weight=k)
-        torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        acc = int(counts[:, 1].sum())
-        out[str(k)] = {"drawn": drawn, "survivors": len(surv), "accepted": acc,
-                       "logical_errors": int(counts[:, 2].sum()), "seconds": dt,
-                       "accepted_shots_per_s": acc / dt if dt > 0 else None,
+        dt, (counts, res) = _timed(lambda: q.mps_sample_batch(circ, surv, p=0.0, seed=args.seed, chi_max=chi,
+                                                              cutoff=args.cutoff, fault_weight=k))
+        acc, err = int(counts[:, 1].sum()), int(counts[:, 2].sum())
+        counts_all[k] = (drawn, acc, err)
+        out[str(k)] = {"drawn": drawn, "survivors": int(surv.numel()), "accepted": acc, "logical_errors": err,
+                       "seconds": dt, "accepted_shots_per_s": acc / dt if dt > 0 else None,
                        "chi_peak": int(res["chi_peak"].max()), "max_discarded": float(res["discarded"].max())}
-    return {"chi_max": chi, "target_survivors_per_k": target, "per_k": out}
+    m = int(circ.info()["n_channels"])
+    curve = {}
+    for pp in (1e-5, 3e-5, 1e-4):
+        pa = stats.profile_interval(counts_all, m, pp, "p_acc")
+        pl = stats.profile_interval(counts_all, m, pp, "p_le")
+        curve[str(pp)] = {"p_acc": [pa["estimate"], pa["lo"], pa["hi"]], "p_le": [pl["estimate"], pl["lo"], pl["hi"]],
+                          "truncation_bound": pa["truncation"]}
+    return {"chi_max": chi, "target_survivors_per_k": target, "per_k": out, "p_curve_R100": curve}
+
+
+def large_bond_rows(q, args, names=("d5_49q_60l_b128", "d5_49q_60l_b256"), shots=(296, 148)):
+    """Config 3 on the large-bond workloads (encoded bond 64, check layers reaching bond 128 / 256 in the
+    exact regime): one device-timed batch of pre-screen survivors per workload (complex64, chi_max 256,
+    cutoff 1e-10), one CTA per shot."""
+    from synth import workload_circuit
+    out = {}
+    for name, n in zip(names, shots):
+        c = q.Circuit(workload_circuit(name, seed=args.seed))
+        pre = q.pauli_prescreen(c, 64 * 70_000_000, int(math.ceil(n / 0.0008 / 64.0)) * 64, p=args.p, seed=args.seed)
+        surv = pre["survivors"][:n]
+        q.mps_sample_batch(c, surv[:1], p=args.p, seed=args.seed, chi_max=256, cutoff=args.cutoff, per_shot=False)
+        dt, (counts, res) = _timed(lambda: q.mps_sample_batch(c, surv, p=args.p, seed=args.seed, chi_max=256,
+                                                              cutoff=args.cutoff, per_shot=True))
+        acc = int(counts[:, 1].sum())
+        flops = float(res["alg_flops"].sum())
+        out[name] = {"survivors": int(surv.numel()), "accepted": acc, "seconds": dt,
+                     "accepted_shots_per_s": acc / dt if dt > 0 else None, "alg_tflops": flops / dt / 1e12 if dt else None,
+                     "chi_peak": int(res["chi_peak"].max()), "max_discarded": float(res["discarded"].max()),
+                     "gmem_updates_per_shot": float(res["gmem_updates"].mean())}
+    return out
 
 
 # ---- the other configurations -------------------------------------------------------------------
@@ -558,6 +586,7 @@ def main():
         return rank_shot0(rank, step, drawn)
 
     kernel_ms = []
+    launch = {}  # the engine's launch configuration (autotuned on the first batch)
     flops_dev = torch.zeros((), dtype=torch.float64, device="cuda")  # summed over the timed steps
     last = {}
 
@@ -569,7 +598,7 @@ def main():
         e0.record(stream)
         counts, _ = q.mps_sample_batch(circ, surv, p=args.p, seed=args.seed, chi_max=args.chi_max,
                                        cutoff=args.cutoff, precision=q.QC_C64, per_shot=True,
-                                       per_shot_buf=shot_buf, copy_back=False)
+                                       per_shot_buf=shot_buf, copy_back=False, launch=launch)
         e1.record(stream)
         if timed:
             kernel_ms.append((e0, e1, int(surv.numel())))
@@ -663,7 +692,7 @@ def main():
     legs = None
     if not args.no_legs:
         legs = {"c1_17q_c128": c1_leg(q, args), "c2_prescreen_1e8": c2_leg(q, args, peaks),
-                "c3_chi_rows": chi_rows_leg(q, circ, args)}
+                "c3_chi_rows": chi_rows_leg(q, circ, args), "c3_large_bond": large_bond_rows(q, args)}
     comparator = None
     if not args.no_comparator:
         comparator = comparator_leg(q, text, circ, int(res["shot"][0]), args)
@@ -698,7 +727,9 @@ def main():
                      "frac": achieved / alu_peak if alu_peak else None, "traffic": engine_traffic(),
                      "traffic_note": "DRAM read+write bytes per engine launch from one ncu capture of this "
                                      "engine source (null when the source changed since)",
-                     "kernel": "engine_kernel<float,32> (one warp per shot)",
+                     "kernel": ("engine_kernel<float,%d> (%s, %d KB work area, autotuned)" % (
+                         launch.get("threads", 0), "one warp per shot" if launch.get("threads") == 32
+                         else "one CTA per shot", launch.get("kb", 0))),
                      "peak_note": peak_note,
                      "flops_note": "algorithmic flops counted per shot by the engine and summed on the device "
                                    "over every timed step",

@@ -212,18 +212,29 @@ qc_status mps_sample_batch(const qc_circuit* circuit, qc_noise noise, const uint
  *   readout_k       columns of readout_p1_dev (0 = no record)
  *   sweep_cap       > 0: Jacobi sweep limit of every split of the shots (default 40 for QC_C64, 60
  *                   for QC_C128); a split that does not converge within it ends its shot with
- *                   per-shot status QC_ENOCONV.  The noiseless reference run keeps the default. */
+ *                   per-shot status QC_ENOCONV.  The noiseless reference run keeps the default.
+ *   phase_cycles_dev  optional device array of 8 counters, ACCUMULATED into: SM clock cycles spent
+ *                   by the shots' engines in each phase (summed over engines): 0 fault draws,
+ *                   1 two-site update up to the SVD (staging, gate fusion, contraction), 2 Jacobi,
+ *                   3 spectrum, truncation and the write-back of both factors, 4 centre moves,
+ *                   5 product-state SWAPs, 6 readouts, 7 the final overlap and the counters.
+ *   launch_threads_out, launch_kb_out  out: the launch configuration of the (first) pass -- threads
+ *                   per shot (32 = one warp per shot) and the work area per shot in KB -- as chosen by
+ *                   the library's autotuner, its rule or the QCMPS_* overrides. */
 typedef struct {
     double* readout_p1_dev;
     int32_t readout_k;
     int32_t sweep_cap;
+    uint64_t* phase_cycles_dev;
+    int32_t launch_threads_out;
+    int32_t launch_kb_out;
 } qc_mps_trace;
 
 /* mps_sample_batch with the verification hooks above (trace may be NULL, which is mps_sample_batch). */
 qc_status mps_sample_batch_traced(const qc_circuit* circuit, qc_noise noise, const uint64_t* shots_dev,
                                   uint64_t nshots, qc_mps_params params, qc_counts* per_w,
                                   int32_t w_max, qc_shot_result* per_shot_dev,
-                                  const qc_mps_trace* trace, void* stream);
+                                  qc_mps_trace* trace, void* stream);
 
 /* Bytes of device memory one in-flight shot needs (site tensors at their capacities plus the
  * per-shot split scratch), the footprint used for admission. */

@@ -54,7 +54,8 @@ class ShotResult(C.Structure):
 
 
 class MpsTrace(C.Structure):
-    _fields_ = [("readout_p1_dev", C.c_void_p), ("readout_k", C.c_int32), ("sweep_cap", C.c_int32)]
+    _fields_ = [("readout_p1_dev", C.c_void_p), ("readout_k", C.c_int32), ("sweep_cap", C.c_int32),
+                ("phase_cycles_dev", C.c_void_p), ("launch_threads_out", C.c_int32), ("launch_kb_out", C.c_int32)]
 
 
 class AluPeaks(C.Structure):

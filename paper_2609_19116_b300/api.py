@@ -113,10 +113,11 @@ def pauli_prescreen(circ: Circuit, shot0: int, nshots: int, *, p: float, seed: i
 def mps_sample_batch(circ: Circuit, shots: torch.Tensor, *, p: float, seed: int, chi_max: int, cutoff: float,
                      precision: int = N.QC_C64, tau: float = 0.0, w_max: int = 15, fault_weight: int = -1,
                      per_shot: bool = True, per_shot_buf: torch.Tensor | None = None, copy_back: bool = True,
-                     stream=None):
+                     launch: dict | None = None, stream=None):
     """Returns (counts[w_max+1, 3] numpy uint64 (n, n_acc, n_err), per-shot structured array or None).
 
-    With copy_back=False the per-shot results stay in per_shot_buf on the device."""
+    With copy_back=False the per-shot results stay in per_shot_buf on the device.  launch: optional dict
+    that receives the launch configuration of the first pass (threads per shot, KB of work area)."""
     shots = _dev_u64(shots)
     n = shots.numel()
     counts = (N.Counts * (w_max + 1))()
@@ -125,8 +126,15 @@ def mps_sample_batch(circ: Circuit, shots: torch.Tensor, *, p: float, seed: int,
         buf = per_shot_buf if per_shot_buf is not None else torch.zeros(
             max(n, 1) * SHOT_DTYPE.itemsize, dtype=torch.uint8, device=shots.device)
     prm = N.MpsParams(chi_max, cutoff, precision, tau)
-    N.check(N.lib().mps_sample_batch(circ.handle, N.Noise(p, seed, fault_weight), _ptr(shots), n, prm,
-                                     C.cast(counts, C.c_void_p), w_max, _ptr(buf), _stream(stream)))
+    if launch is None:
+        N.check(N.lib().mps_sample_batch(circ.handle, N.Noise(p, seed, fault_weight), _ptr(shots), n, prm,
+                                         C.cast(counts, C.c_void_p), w_max, _ptr(buf), _stream(stream)))
+    else:
+        tr = N.MpsTrace(None, 0, 0, None)
+        N.check(N.lib().mps_sample_batch_traced(circ.handle, N.Noise(p, seed, fault_weight), _ptr(shots), n, prm,
+                                                C.cast(counts, C.c_void_p), w_max, _ptr(buf), C.byref(tr),
+                                                _stream(stream)))
+        launch.update(threads=tr.launch_threads_out, kb=tr.launch_kb_out)
     arr = np.array([[c.n, c.n_acc, c.n_err] for c in counts], dtype=np.uint64)
     res = None
     if per_shot and copy_back:
@@ -136,15 +144,19 @@ def mps_sample_batch(circ: Circuit, shots: torch.Tensor, *, p: float, seed: int,
 
 def mps_sample_batch_traced(circ: Circuit, shots: torch.Tensor, *, p: float, seed: int, chi_max: int, cutoff: float,
                             precision: int = N.QC_C64, tau: float = 0.0, w_max: int = 15, fault_weight: int = -1,
-                            readout_k: int = 0, sweep_cap: int = 0, stream=None):
+                            readout_k: int = 0, sweep_cap: int = 0, phase_cycles: torch.Tensor | None = None,
+                            launch: dict | None = None, stream=None):
     """mps_sample_batch with the verification hooks: returns (counts, per-shot results, readout
-    probabilities [nshots, readout_k] as a float64 numpy array, NaN after a shot's end)."""
+    probabilities [nshots, readout_k] as a float64 numpy array, NaN after a shot's end).  phase_cycles:
+    optional CUDA int64 tensor of 8 counters that the call adds the engines' cycles per phase to; launch:
+    optional dict that receives the launch configuration of the first pass (threads per shot, KB)."""
     shots = _dev_u64(shots)
     n = shots.numel()
     counts = (N.Counts * (w_max + 1))()
     buf = torch.zeros(max(n, 1) * SHOT_DTYPE.itemsize, dtype=torch.uint8, device=shots.device)
     p1 = torch.empty(max(n * readout_k, 1), dtype=torch.float64, device=shots.device)
-    tr = N.MpsTrace(p1.data_ptr() if readout_k > 0 else None, readout_k, sweep_cap)
+    tr = N.MpsTrace(p1.data_ptr() if readout_k > 0 else None, readout_k, sweep_cap,
+                    _dev_u64(phase_cycles).data_ptr() if phase_cycles is not None else None)
     prm = N.MpsParams(chi_max, cutoff, precision, tau)
     N.check(N.lib().mps_sample_batch_traced(circ.handle, N.Noise(p, seed, fault_weight), _ptr(shots), n, prm,
                                             C.cast(counts, C.c_void_p), w_max, _ptr(buf), C.byref(tr),
@@ -152,6 +164,8 @@ def mps_sample_batch_traced(circ: Circuit, shots: torch.Tensor, *, p: float, see
     arr = np.array([[c.n, c.n_acc, c.n_err] for c in counts], dtype=np.uint64)
     res = np.frombuffer(buf[: n * SHOT_DTYPE.itemsize].cpu().numpy().tobytes(), dtype=SHOT_DTYPE)
     rec = p1[: n * readout_k].cpu().numpy().reshape(n, readout_k) if readout_k > 0 else None
+    if launch is not None:
+        launch.update(threads=tr.launch_threads_out, kb=tr.launch_kb_out)
     return arr, res, rec
 
 

@@ -91,6 +91,7 @@ struct EngineParams {
     int* ref_dims_out;    // reference run: bond dims [nq+1]
     double* ref_disc_out;
     int sweep_cap;
+    unsigned long long* phase_cycles;  // optional [8]: SM cycles per phase of the shots, summed
     double* trace_p1;          // optional [ntasks x trace_k]: readout probabilities of each shot
     const uint64_t* trace_pos; // optional: record row of each task (the capacity re-run pass)
     int trace_k;
@@ -110,6 +111,8 @@ struct Shared {
     int* nf;      // fault count of the current shot
     V* big;       // warp mode: the CTA's shared work area for updates too large for X
     int* big_lock;
+    unsigned long long* phase;  // [8] cycles per phase of this engine's current shot (thread 0)
+    long long* t_mark;          // start of the current phase
 };
 
 template <typename R>
@@ -188,6 +191,19 @@ struct Engine {
     }
 
     __device__ V* site(int q) { return slot + P.off[q]; }
+
+    // Phase timing (verification hook): thread 0 charges the SM cycles since the last mark to phase k.
+    enum { PH_FAULTS, PH_CONTRACT, PH_JACOBI, PH_SPLIT_OUT, PH_MOVE, PH_PSWAP, PH_READOUT, PH_FINISH };
+    __device__ __forceinline__ void tick() {
+        if (P.phase_cycles && tid_ == 0) *S.t_mark = clock64();
+    }
+    __device__ __forceinline__ void tock(int k) {
+        if (P.phase_cycles && tid_ == 0) {
+            const long long t = clock64();
+            S.phase[k] += (unsigned long long)(t - *S.t_mark);
+            *S.t_mark = t;
+        }
+    }
 
     // ---- single-qubit gates are deferred: pend[q] <- g pend[q] (thread 0 only; consumers start
     //      with a barrier).  A gate on the physical index keeps the canonical form, so it can wait
@@ -578,6 +594,7 @@ struct Engine {
     // and A, B are read from the site tensors.
     __device__ void update(int q, const V* g, bool right) {
         bsync<NT>();  // pending gates written by thread 0, dims of the previous update
+        tick();
         const int cl = S.dims[q], cm = S.dims[q + 1], cr = S.dims[q + 2];
         const int m = 2 * cl, n = 2 * cr;
         // the Jacobi orthogonalises the columns of theta' (xt) or of theta'^H, whichever has fewer
@@ -695,11 +712,13 @@ struct Engine {
         const int bw = (int)(P.x_smem / (2 * (uint32_t)(rows + 1))) & ~1;  // even: every block pairs up
         const bool blocked = (X == xg) && bw >= 2 && bw * 2 < cols;
         gmem_updates += (X == xg) ? 1 : 0;
+        tock(PH_CONTRACT);
         if (!(blocked ? jacobi_blocked(X, rows, cols, ld, floor2, S.X, bw) : jacobi(X, rows, cols, ld, floor2))) {
             status = QC_ENOCONV;
             release_big(locked);
             return;
         }
+        tock(PH_JACOBI);
         const int r = spectrum(X, rows, cols, ld, sig2, perm, floor2);
         const R scale = (R)S.red[41];
         if (r > P.cap[q + 1]) {
@@ -787,6 +806,7 @@ struct Engine {
         release_big(locked);
         if (tid_ == 0) S.dims[q + 1] = r;
         bsync<NT>();
+        tock(PH_SPLIT_OUT);
         chi_peak = max(chi_peak, r);
         ++nupd;
         if (tid_ == 0) {  // integer accounting: the FP64 pipe is narrow on this part
@@ -888,6 +908,7 @@ struct Engine {
     // orthogonality centre is a gauge change).
     __device__ void move(int q, bool right) {
         bsync<NT>();
+        tick();
         const int cl = S.dims[q], cm = S.dims[q + 1], cr = S.dims[q + 2];
         const int m = 2 * cl, n = 2 * cr;
         const int rows = right ? m : n;
@@ -971,6 +992,7 @@ struct Engine {
         bsync<NT>();
         if (tid_ == 0) S.dims[q + 1] = r;
         bsync<NT>();
+        tock(PH_MOVE);
         ++nupd;
         if (tid_ == 0) {  // Householder QR count of the rows x cm factor, plus the product with R
             const unsigned long long M = max(rows, cm), K = min(rows, cm);
@@ -991,6 +1013,7 @@ struct Engine {
     // orthonormal factor on the product qubit's new site, which keeps the canonical form.
     __device__ void pswap(int q, bool prod_left) {
         bsync<NT>();
+        tick();
         const int cl = S.dims[q], cm = S.dims[q + 1], cr = S.dims[q + 2];
         V* A = site(q);
         V* B = site(q + 1);
@@ -1115,6 +1138,7 @@ struct Engine {
             flops += 16ull * cl * cm * cr;
         }
         bsync<NT>();
+        tock(PH_PSWAP);
         chi_peak = max(chi_peak, nb);
     }
 
@@ -1122,6 +1146,7 @@ struct Engine {
     // returns the outcome, or -1 when the shot ends (rejected / error)
     __device__ int readout(int q, uint32_t rid, bool is_meas, uint64_t shot, int64_t src) {
         bsync<NT>();  // pending gates written by thread 0
+        tick();
         const int cl = S.dims[q], cr = S.dims[q + 1];
         V* a = site(q);
         const V* u = S.pend + q * 4;
@@ -1186,6 +1211,7 @@ struct Engine {
             else { *x0 = cmk<V>(0, 0); *x1 = kv; }
         }
         bsync<NT>();
+        tock(PH_READOUT);
         return outcome;
     }
 
@@ -1311,8 +1337,12 @@ struct Engine {
             a[1] = cmk<V>(0, 0);
             reset_pend(q);
         }
+        if (P.phase_cycles && tid_ == 0)
+            for (int k = 0; k < 8; ++k) S.phase[k] = 0;
         bsync<NT>();
+        tick();
         const int nf = faults(shot);
+        tock(PH_FAULTS);
         if (nf > MAXF) status = QC_ECAPACITY;
         for (uint32_t base = 0; base < P.nops && status == 0; base += OPCH) {
             const uint32_t cnt = min((uint32_t)OPCH, P.nops - base);
@@ -1362,6 +1392,7 @@ struct Engine {
             bsync<NT>();
         }
         // finish: apply the gates still pending, then compare with the reference
+        tick();
         if (status == 0)
             for (int q = 0; q < P.nq; ++q) {
                 bsync<NT>();
@@ -1416,6 +1447,9 @@ struct Engine {
                 }
             }
         }
+        tock(PH_FINISH);
+        if (P.phase_cycles && tid_ == 0 && !P.reference)
+            for (int k = 0; k < 8; ++k) atomicAdd(&P.phase_cycles[k], S.phase[k]);
         bsync<NT>();
     }
 };
@@ -1437,6 +1471,8 @@ __device__ unsigned char* carve(Shared<R>& S, unsigned char* p, const EnginePara
     S.gate = reinterpret_cast<V*>(p); p += 16 * sizeof(V);
     S.fch = reinterpret_cast<uint32_t*>(p); p += MAXF * sizeof(uint32_t);
     S.nf = reinterpret_cast<int*>(p); p += 16;
+    S.phase = reinterpret_cast<unsigned long long*>(p); p += 8 * sizeof(unsigned long long);
+    S.t_mark = reinterpret_cast<long long*>(p); p += 16;
     S.fcode = reinterpret_cast<uint8_t*>(p); p += MAXF;
     return reinterpret_cast<unsigned char*>(((uintptr_t)p + 15) & ~(uintptr_t)15);
 }
@@ -1481,7 +1517,7 @@ __host__ __device__ size_t engine_smem(const EngineParams<R>& P) {
     using V = typename VecOf<R>::T;
     return (size_t)P.x_smem * sizeof(V) + OPCH * sizeof(MpsOp) + 64 * sizeof(double) +
            (size_t)(P.nq + 1) * sizeof(int) + 16 + (size_t)P.nq * 4 * sizeof(V) + 16 * sizeof(V) +
-           MAXF * sizeof(uint32_t) + 16 + MAXF + 16;
+           MAXF * sizeof(uint32_t) + 16 + 8 * sizeof(unsigned long long) + 16 + MAXF + 16;
 }
 
 // ---- gate tables ------------------------------------------------------------------------------
@@ -1613,12 +1649,22 @@ static size_t configure_smem(EngineParams<R>& P, size_t budget, uint64_t x_full)
     return engine_smem<R, NT>(P);
 }
 
+// Launch configuration of the persistent engine: threads per shot (32 = one warp per shot, several
+// shot slots per SM; 128 / 256 / 512 = one CTA per shot) and the shared-memory work area per engine.
+struct LaunchCfg {
+    int variant;  // 32, 128, 256 or 512 (the large CTA)
+    int kb;       // work area per engine, KB
+    int warps;    // warp variant: engines per CTA sharing a large area (1 = none)
+    int big_kb;   // warp variant: the shared large area, KB
+};
+
 // One persistent launch over `nshots` shots with slots of layout L (reference stored in L).
 template <typename R, int NT_BIG>
 static qc_status run_pass(CircuitImpl& c, EngineParams<R> P, const SlotLayout& L, const void* ref_state,
                           const int* cap_dev, const uint64_t* off_dev, const RefState& ref,
                           const uint64_t* shots_dev, uint64_t nshots, unsigned long long* counts_dev,
-                          qc_shot_result* per_shot, cudaStream_t s, int max_slots, int nsm, bool defer) {
+                          qc_shot_result* per_shot, cudaStream_t s, int max_slots, int nsm, bool defer,
+                          LaunchCfg cfg) {
     using V = typename VecOf<R>::T;
     const int chi = P.chi_max;
     P.ref_chi = std::max(1, ref.chi_peak);
@@ -1631,27 +1677,8 @@ static qc_status run_pass(CircuitImpl& c, EngineParams<R> P, const SlotLayout& L
     P.scratch_stride = scratch_stride;
     P.xg_elems = xg_elems;
     P.defer_capacity = defer ? 1 : 0;
-    // the variant (threads per shot, shared-memory budget per shot) follows the reference run's
-    // chi_peak and the batch size; QCMPS_ENGINE = warp | cta128 | cta256 | cta and QCMPS_SMEM_KB,
-    // QCMPS_WARPS, QCMPS_BIG_KB override it for tuning.
-    const char* force = getenv("QCMPS_ENGINE");
-    // throughput mode (one warp per shot) needs many shots to fill the SMs; a batch with no more
-    // shots than SMs runs in latency mode (one CTA per shot) unless the caller shares the GPU with
-    // other batches (the serving loop), where throughput mode keeps more shots in flight
-    // The warp variant only for passes whose slot capacity keeps theta at most 128 x 128: a pass at a
-    // larger capacity (the re-run of shots that outgrew the bucket) would run 256-wide or larger splits
-    // in one warp.  Such a pass takes the 128-thread CTA variant when it shares the GPU (72 KB of shared
-    // memory finds room beside other batches' warps) and the 512-thread one otherwise.
-    const bool small = P.chi_max <= 64 && ref.chi_peak <= 64;
-    int variant = (small && (nshots > (uint64_t)nsm || P.shared_gpu)) ? 32 : (P.shared_gpu ? 128 : NT_BIG);
-    if (force && !strcmp(force, "warp")) variant = 32;
-    if (force && !strcmp(force, "cta128")) variant = 128;
-    if (force && !strcmp(force, "cta256")) variant = 256;
-    if (force && !strcmp(force, "cta")) variant = NT_BIG;
-    const char* kb = getenv("QCMPS_SMEM_KB");
-    const int kbv = kb ? atoi(kb) : 0;
-    const char* wv = getenv("QCMPS_WARPS");
-    const char* bv = getenv("QCMPS_BIG_KB");
+    const int variant = cfg.variant;
+    const int kbv = cfg.kb;
     size_t smem;
     int nt = variant;
     int engines = 1;  // engines (shot slots) per CTA
@@ -1660,10 +1687,10 @@ static qc_status run_pass(CircuitImpl& c, EngineParams<R> P, const SlotLayout& L
         // measured on the 49-qubit workload: one warp per CTA with 24 KB (9 shot slots per SM)
         // beats sharing a large area between warps (contention) and larger per-warp areas (fewer
         // slots)
-        engines = (wv && atoi(wv) >= 1 && atoi(wv) <= 8) ? atoi(wv) : 1;
+        engines = (cfg.warps >= 1 && cfg.warps <= 8) ? cfg.warps : 1;
         const size_t per = configure_smem<R, 32>(P, (kbv >= 8 && kbv <= 200 ? kbv : 24) * 1024, xg_elems);
         const size_t region = (per + 15) & ~(size_t)15;
-        const size_t big_budget = (bv && atoi(bv) >= 0) ? (size_t)atoi(bv) * 1024 : 0;
+        const size_t big_budget = cfg.big_kb > 0 ? (size_t)cfg.big_kb * 1024 : 0;
         size_t room = 227 * 1024 > region * engines + 16 ? 227 * 1024 - region * engines - 16 : 0;
         if (engines == 1) room = 0;  // nobody to share with
         room = std::min(room, big_budget);
@@ -1678,7 +1705,7 @@ static qc_status run_pass(CircuitImpl& c, EngineParams<R> P, const SlotLayout& L
         smem = configure_smem<R, 256>(P, (kbv >= 8 && kbv <= 200 ? kbv : 100) * 1024, xg_elems);
         fn = (const void*)engine_kernel<R, 256>;
     } else {
-        smem = configure_smem<R, NT_BIG>(P, 200 * 1024, xg_elems);
+        smem = configure_smem<R, NT_BIG>(P, (kbv >= 8 && kbv <= 220 ? kbv : 200) * 1024, xg_elems);
         fn = (const void*)engine_kernel<R, NT_BIG>;
         nt = NT_BIG;
     }
@@ -1732,6 +1759,102 @@ static qc_status run_pass(CircuitImpl& c, EngineParams<R> P, const SlotLayout& L
     return out;
 }
 
+// The launch rule without measurement: one warp per shot (24 KB work area) for small passes (the first
+// pass of a circuit whose noiseless run stays at bond 64) when the batch fills the SMs or shares the GPU
+// with other batches; otherwise one CTA per shot -- 128 threads with 72 KB when sharing the GPU (it finds
+// room beside other batches' warps), else 512 threads with 200 KB (the lowest latency per shot).  The
+// re-run pass of shots that outgrew the capacity bucket is never small: in one warp it would run 256-wide
+// or larger splits.
+static LaunchCfg rule_cfg(bool small, uint64_t nshots, int nsm, bool shared_gpu, int nt_big) {
+    if (small && (nshots > (uint64_t)nsm || shared_gpu)) return LaunchCfg{32, 24, 1, 0};
+    if (shared_gpu) return LaunchCfg{128, 72, 1, 0};
+    return LaunchCfg{nt_big, 200, 1, 0};
+}
+
+// Manual overrides for tuning and tests: QCMPS_ENGINE = warp | cta128 | cta256 | cta, QCMPS_SMEM_KB
+// (work area per engine), QCMPS_WARPS (engines per CTA), QCMPS_BIG_KB (their shared area).  Returns true
+// when any is set (the configuration is then not tuned).
+static bool env_cfg(LaunchCfg& cfg, int nt_big) {
+    bool any = false;
+    if (const char* f = getenv("QCMPS_ENGINE")) {
+        any = true;
+        if (!strcmp(f, "warp")) cfg = LaunchCfg{32, 24, 1, 0};
+        else if (!strcmp(f, "cta128")) cfg = LaunchCfg{128, 72, 1, 0};
+        else if (!strcmp(f, "cta256")) cfg = LaunchCfg{256, 100, 1, 0};
+        else if (!strcmp(f, "cta")) cfg = LaunchCfg{nt_big, 200, 1, 0};
+    }
+    if (const char* k = getenv("QCMPS_SMEM_KB")) { any = true; cfg.kb = atoi(k); }
+    if (const char* w = getenv("QCMPS_WARPS")) { any = true; cfg.warps = atoi(w); }
+    if (const char* b = getenv("QCMPS_BIG_KB")) { any = true; cfg.big_kb = atoi(b); }
+    return any;
+}
+
+// Measured choice of the launch configuration (autotuner).  On the first batch of a (device, slot
+// capacity, precision, size class) of a circuit, every candidate runs the shots' first eighth of the
+// site-operation program on enough shots for about two rounds of its slots (results discarded), timed with
+// CUDA events on the caller's stream; the configuration with the most shots per second is cached in the
+// circuit and used from then on.  Candidates: for small capacities the warp variant at 20 / 24 / 28 / 32
+// KB and the 128- and 256-thread CTAs; for large capacities the 512-, 256- and 128-thread CTAs.
+template <typename R, int NT_BIG>
+static qc_status run_pass(CircuitImpl& c, EngineParams<R> P, const SlotLayout& L, const void* ref_state,
+                          const int* cap_dev, const uint64_t* off_dev, const RefState& ref,
+                          const uint64_t* shots_dev, uint64_t nshots, unsigned long long* counts_dev,
+                          qc_shot_result* per_shot, cudaStream_t s, int max_slots, int nsm, bool defer,
+                          LaunchCfg cfg);
+
+template <typename R, int NT_BIG>
+static LaunchCfg tuned_cfg(CircuitImpl& c, const EngineParams<R>& P, const SlotLayout& L, const void* ref_state,
+                           const int* cap_dev, const uint64_t* off_dev, const RefState& ref, const uint64_t* shots_dev,
+                           uint64_t nshots, cudaStream_t s, int nsm, int dev, bool small, LaunchCfg fallback) {
+    const std::array<int, 4> key{dev, P.chi_max, P.precision, small ? 1 : 0};
+    std::lock_guard<std::mutex> lk(c.tune_mu);
+    auto it = c.tuned.find(key);
+    if (it != c.tuned.end()) return LaunchCfg{it->second[0], it->second[1], 1, 0};
+    std::vector<LaunchCfg> cand;
+    if (small) cand = {{32, 20, 1, 0}, {32, 24, 1, 0}, {32, 28, 1, 0}, {32, 32, 1, 0}, {128, 72, 1, 0}, {256, 100, 1, 0}};
+    else cand = {{NT_BIG, 200, 1, 0}, {256, 100, 1, 0}, {128, 72, 1, 0}};
+    unsigned long long* scratch = nullptr;
+    const size_t cb = 3 * (size_t)(P.wmax + 1) * sizeof(unsigned long long);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaMallocAsync((void**)&scratch, cb, s) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+        cudaEventCreate(&e1) != cudaSuccess) {
+        cudaGetLastError();
+        if (scratch) cudaFreeAsync(scratch, s);
+        return fallback;
+    }
+    EngineParams<R> Pc = P;
+    Pc.nops = std::max<uint32_t>(OPCH, P.nops / 8);
+    Pc.per_shot = nullptr;
+    Pc.trace_p1 = nullptr;
+    Pc.trace_pos = nullptr;
+    Pc.phase_cycles = nullptr;
+    Pc.counts = scratch;
+    const uint64_t tasks = std::min<uint64_t>(nshots, (small ? 18ull : 2ull) * (uint64_t)nsm);
+    LaunchCfg best = fallback;
+    double best_rate = -1.0;
+    for (const LaunchCfg& cf : cand) {
+        cudaEventRecord(e0, s);
+        const qc_status st = run_pass<R, NT_BIG>(c, Pc, L, ref_state, cap_dev, off_dev, ref, shots_dev, tasks, scratch,
+                                                 nullptr, s, 0, nsm, true, cf);
+        cudaEventRecord(e1, s);
+        float ms = 0;
+        if (st != QC_OK || cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        const double rate = ms > 0 ? (double)tasks / ms : 0.0;
+        if (rate > best_rate) {
+            best_rate = rate;
+            best = cf;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFreeAsync(scratch, s);
+    c.tuned[key] = {best.variant, best.kb};
+    return best;
+}
+
 // Host driver shared by mps_sample_batch and the serving loop.
 //
 // chi-bucketed variants: the reference run tells the bond dimensions the circuit reaches.  When
@@ -1742,7 +1865,7 @@ template <typename R, int NT_BIG>
 static qc_status run_engine(CircuitImpl& c, qc_noise noise, const uint64_t* shots_dev, uint64_t nshots,
                             qc_mps_params prm, unsigned long long* counts_dev, int wmax,
                             qc_shot_result* per_shot, cudaStream_t s, int max_slots, bool shared_gpu,
-                            const qc_mps_trace* trace) {
+                            qc_mps_trace* trace) {
     using V = typename VecOf<R>::T;
     DeviceCopy* dc;
     qc_status st = c.device_copy(&dc);
@@ -1876,6 +1999,7 @@ static qc_status run_engine(CircuitImpl& c, qc_noise noise, const uint64_t* shot
     }
     if (nshots == 0) return QC_OK;
     if (trace && trace->sweep_cap > 0) P.sweep_cap = trace->sweep_cap;
+    if (trace && trace->phase_cycles_dev) P.phase_cycles = reinterpret_cast<unsigned long long*>(trace->phase_cycles_dev);
     if (trace && trace->readout_p1_dev && trace->readout_k > 0) {
         P.trace_p1 = trace->readout_p1_dev;
         P.trace_k = trace->readout_k;
@@ -1884,9 +2008,25 @@ static qc_status run_engine(CircuitImpl& c, qc_noise noise, const uint64_t* shot
     // 2. capacity bucket: slots sized for chi_alloc = min(chi, max(64, 2 chi_peak_ref)); a shot
     //    that outgrows it is reported by the first pass and re-run with full capacity
     const int chi_alloc = bucket_chi(ref->chi_peak, chi);
-    if (chi_alloc >= chi)
+    // launch configuration: manual override, else the measured choice (batches that fill the GPU on
+    // their own), else the rule
+    // (the first pass is small when the noiseless run stays at bond 64, as most shots do; the re-run
+    // pass holds exactly the shots that outgrew the bucket, so it is large)
+    auto pick = [&](const EngineParams<R>& Pp, const SlotLayout& Lp, const int* cp, const uint64_t* op,
+                    uint64_t n, bool first) {
+        const bool small = first && ref->chi_peak <= 64;
+        LaunchCfg cf = rule_cfg(small, n, nsm, shared_gpu, NT_BIG);
+        if (env_cfg(cf, NT_BIG)) return cf;
+        if (first && !shared_gpu && n >= 2ull * (uint64_t)nsm && !getenv("QCMPS_NO_TUNE"))
+            cf = tuned_cfg<R, NT_BIG>(c, Pp, Lp, ref->state, cp, op, *ref, shots_dev, n, s, nsm, dev, small, cf);
+        return cf;
+    };
+    if (chi_alloc >= chi) {
+        const LaunchCfg cf = pick(P, L, ref->cap, ref->off, nshots, true);
+        if (trace) { trace->launch_threads_out = cf.variant; trace->launch_kb_out = cf.kb; }
         return run_pass<R, NT_BIG>(c, P, L, ref->state, ref->cap, ref->off, *ref, shots_dev, nshots, counts_dev,
-                                   per_shot, s, max_slots, nsm, false);
+                                   per_shot, s, max_slots, nsm, false, cf);
+    }
     const SlotLayout L1 = slot_layout(c.n, chi_alloc);
     int* cap1 = nullptr;
     uint64_t* off1 = nullptr;
@@ -1913,8 +2053,10 @@ static qc_status run_engine(CircuitImpl& c, qc_noise noise, const uint64_t* shot
     if (!res1) QC_CUDA(cudaMallocAsync((void**)&res1, nshots * sizeof(qc_shot_result), s));
     EngineParams<R> P1 = P;
     P1.chi_max = chi_alloc;
+    const LaunchCfg cf1 = pick(P1, L1, cap1, off1, nshots, true);
+    if (trace) { trace->launch_threads_out = cf1.variant; trace->launch_kb_out = cf1.kb; }
     qc_status out = run_pass<R, NT_BIG>(c, P1, L1, ref->state, cap1, off1, *ref, shots_dev, nshots, counts_dev, res1,
-                                        s, max_slots, nsm, true);
+                                        s, max_slots, nsm, true, cf1);
     std::vector<qc_shot_result> h;
     if (out == QC_OK) {
         h.resize(nshots);
@@ -1941,7 +2083,7 @@ static qc_status run_engine(CircuitImpl& c, qc_noise noise, const uint64_t* shot
         P2.trace_pos = pos2;
         if (out == QC_OK)
             out = run_pass<R, NT_BIG>(c, P2, L, ref->state, ref->cap, ref->off, *ref, shots2, redo.size(), counts_dev,
-                                      res2, s, max_slots, nsm, false);
+                                      res2, s, max_slots, nsm, false, pick(P2, L, ref->cap, ref->off, redo.size(), false));
         if (out == QC_OK && per_shot) {
             std::vector<qc_shot_result> h2(redo.size());
             e = cudaMemcpyAsync(h2.data(), res2, h2.size() * sizeof(qc_shot_result), cudaMemcpyDeviceToHost, s);
@@ -1961,7 +2103,7 @@ static qc_status run_engine(CircuitImpl& c, qc_noise noise, const uint64_t* shot
 
 qc_status engine_launch(CircuitImpl& c, qc_noise noise, const uint64_t* shots_dev, uint64_t nshots,
                         qc_mps_params prm, unsigned long long* counts_dev, int wmax, qc_shot_result* per_shot,
-                        cudaStream_t s, int max_slots, bool shared_gpu, const qc_mps_trace* trace) {
+                        cudaStream_t s, int max_slots, bool shared_gpu, qc_mps_trace* trace) {
     if (!(noise.p >= 0.0 && noise.p < 1.0)) return fail(QC_EINVAL, "p must lie in [0, 1)");
     if (prm.chi_max < 1) return fail(QC_EINVAL, "chi_max must be >= 1");
     if (!(prm.cutoff >= 0.0)) return fail(QC_EINVAL, "cutoff must be >= 0");
@@ -2018,7 +2160,7 @@ qc_status bucket_footprint(CircuitImpl& c, qc_noise noise, qc_mps_params prm, cu
 
 extern "C" qc_status mps_sample_batch_traced(const qc_circuit* circuit, qc_noise noise, const uint64_t* shots_dev,
                                              uint64_t nshots, qc_mps_params params, qc_counts* per_w, int32_t w_max,
-                                             qc_shot_result* per_shot_dev, const qc_mps_trace* trace, void* stream) {
+                                             qc_shot_result* per_shot_dev, qc_mps_trace* trace, void* stream) {
     if (!circuit) return fail(QC_EINVAL, "null circuit");
     if (w_max < 0 || w_max > 4095) return fail(QC_EINVAL, "w_max must lie in [0, 4095]");
     if (trace && trace->readout_k < 0) return fail(QC_EINVAL, "readout_k must be >= 0");

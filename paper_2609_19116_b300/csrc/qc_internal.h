@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <array>
 #include <cstdint>
 #include <map>
 #include <memory>
@@ -100,6 +101,8 @@ struct CircuitImpl {
     std::map<int, DeviceCopy> dev;  // per device
     std::mutex ref_mu;
     std::map<RefKey, RefState> refs;
+    std::mutex tune_mu;
+    std::map<std::array<int, 4>, std::array<int, 2>> tuned;  // (device, capacity, precision, small) -> launch
     ~CircuitImpl();
     // Upload the programs to the current device once; returns the device copy.
     qc_status device_copy(DeviceCopy** out);
@@ -132,7 +135,7 @@ qc_status prescreen_run(CircuitImpl& c, qc_noise noise, uint64_t shot0, uint64_t
                         cudaStream_t s);
 qc_status engine_launch(CircuitImpl& c, qc_noise noise, const uint64_t* shots_dev, uint64_t nshots,
                         qc_mps_params prm, unsigned long long* counts_dev, int wmax, qc_shot_result* per_shot,
-                        cudaStream_t s, int max_slots, bool shared_gpu, const qc_mps_trace* trace = nullptr);
+                        cudaStream_t s, int max_slots, bool shared_gpu, qc_mps_trace* trace = nullptr);
 qc_status shot_footprint(const CircuitImpl& c, qc_mps_params prm, uint64_t* bytes);
 // Bytes of one shot slot of the first pass (the capacity bucket the engine allocates), computing and
 // caching the noiseless reference state on `s` if needed.

@@ -51,7 +51,8 @@ def _t_placements(rng, n, layers, t_per_layer, t_total):
 
 def cultivation_circuit(n_data: int, layers: int, *, seed: int = 0, t_per_layer: int | None = None,
                         t_total: int | None = None, enc_rounds: int = 4, enc_density: float = 0.75, enc_mix: float = 0.5,
-                        data_cx_prob: float = 0.5, far_prob: float = 0.5, noise: bool = True) -> str:
+                        data_cx_prob: float = 0.5, far_prob: float = 0.5, noise: bool = True,
+                        prefix_layers: int | None = None) -> str:
     """Return the circuit text of a seeded cultivation-shaped circuit.
 
     n_data       data qubits (the line has 2*n_data-1 qubits)
@@ -61,6 +62,8 @@ def cultivation_circuit(n_data: int, layers: int, *, seed: int = 0, t_per_layer:
     enc_rounds   brickwork rounds of the encoding stage (bounds the data entanglement)
     enc_density  probability of a CNOT on each brickwork pair
     enc_mix      probability of an H or S on each data qubit after each brickwork round
+    prefix_layers  emit only the first prefix_layers check layers of this circuit (all random draws
+                 are made as for the full circuit, so the result is a true prefix of it)
     """
     if n_data < 2:
         raise ValueError("need at least two data qubits")
@@ -100,7 +103,10 @@ def cultivation_circuit(n_data: int, layers: int, *, seed: int = 0, t_per_layer:
 
     placed = _t_placements(rng, n, layers, t_per_layer, t_total)
 
+    emit = layers if prefix_layers is None else max(0, min(layers, prefix_layers))
     for layer in range(layers):
+        if layer == emit:  # the remaining layers are drawn (same random sequence) but not emitted
+            keep = len(out)
         out.append("TICK")
         out.append(f"# layer {layer}")
         frame = ["H" if rng.random() < 0.5 else "S" for _ in data]
@@ -153,6 +159,8 @@ def cultivation_circuit(n_data: int, layers: int, *, seed: int = 0, t_per_layer:
             out.append(f"R {a}")
             if noise:
                 out.append(f"XERR {a}")
+    if emit < layers:
+        out = out[:keep]
     return "\n".join(out) + "\n"
 
 
@@ -165,6 +173,11 @@ WORKLOADS = {
     # 49 qubits (25 data + 24 ancilla), 60 layers, 16 T in total: batched MPS workload;
     # noiseless chi_peak 64
     "d5_49q_60l": dict(n_data=25, layers=60, t_total=16, enc_rounds=12, enc_density=1.0, enc_mix=1.0),
+    # the same shape with a deeper encoding, so that the data register carries more entanglement:
+    # the encoded stabiliser state has bond 64 at the middle and the check layers reach bond 128
+    # (24 rounds) or 256 (28 rounds), all exact at chi_max 256
+    "d5_49q_60l_b128": dict(n_data=25, layers=60, t_total=16, enc_rounds=24, enc_density=1.0, enc_mix=1.0),
+    "d5_49q_60l_b256": dict(n_data=25, layers=60, t_total=16, enc_rounds=28, enc_density=1.0, enc_mix=1.0),
 }
 
 

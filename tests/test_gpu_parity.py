@@ -4,8 +4,9 @@
   shots than SMs, complex64, chi_max 256, cutoff 1e-10): there every 64-wide theta is rotated in
   global memory by the blocked Jacobi.  Fidelity and every readout probability at 1e-4 absolute
   (the complex64 tolerance), on shots sampled across the batch.
-* The blocked Jacobi forced at complex128 (a small shared-memory work area) on the 49-qubit
-  workload's 6-layer prefix: fidelity and readout probabilities at 1e-10.
+* The blocked Jacobi forced at complex128 (a small shared-memory work area) on a 6-layer circuit
+  of the 49-qubit workload's shape: fidelity and readout probabilities at 1e-10.
+* The large-bond workloads (check layers up to bond 128 and 256) on their true 2-layer prefixes.
 * Per-readout Born probabilities of the default (one CTA per shot) complex128 engine at 1e-10.
 * Logical-error and acceptance rates of the 17-qubit, 1,000-shot configuration against the
   oracle's own pre-screen + MPS pipeline, within binomial intervals.
@@ -59,7 +60,8 @@ def _compare(res, rec, ref, ftol, ptol, allow_flip=0):
 
 def test_benchmark_launch_warp_engine_blocked_jacobi_c64():
     """The benchmark's kernel and launch (one warp per shot, 24 KB work area, capacity bucket 64) on a
-    10-layer prefix of the 49-qubit workload; 24 shots sampled across a 200-shot batch."""
+    10-layer circuit of the 49-qubit workload's shape (its own seeded draw, which reaches 64-wide
+    theta early); 24 shots sampled across a 200-shot batch."""
     q = lib_ready()
     text = workload_circuit("d5_49q_60l", layers=10)
     c = q.Circuit(text)
@@ -81,7 +83,7 @@ def test_benchmark_launch_warp_engine_blocked_jacobi_c64():
 
 
 def test_blocked_jacobi_forced_c128(monkeypatch):
-    """A 12 KB work area per warp at complex128 on a 6-layer prefix of the 49-qubit workload: every
+    """A 12 KB work area per warp at complex128 on a 6-layer circuit of the 49-qubit workload's shape: every
     64-wide theta goes to global memory and is rotated by the blocked Jacobi in blocks of 3 columns
     (12 KB holds ~430 complex128 elements next to the fixed arrays, 2 blocks x 65 rows each fit)."""
     monkeypatch.setenv("QCMPS_ENGINE", "warp")
@@ -185,3 +187,25 @@ def test_sweep_cap_ends_shots_with_enoconv():
     # the same shots with the default limit converge
     counts2, res2 = q.mps_sample_batch(c, shots, p=0.0, seed=3, chi_max=32, cutoff=1e-12, precision=q.QC_C64)
     assert (res2["status"] == 0).all()
+
+
+@pytest.mark.parametrize("name,prec,tol", [("d5_49q_60l_b128", 0, 1e-4), ("d5_49q_60l_b128", 1, 1e-10),
+                                           ("d5_49q_60l_b256", 0, 1e-4)])
+def test_large_bond_workloads_match_oracle(name, prec, tol):
+    """The large-bond workloads (encoded bond 64, check layers up to bond 128 / 256) on their true
+    2-layer prefix: one CTA per shot with the theta of the widest splits in global memory; fidelity and
+    every readout probability against the oracle."""
+    q = lib_ready()
+    text = workload_circuit(name, prefix_layers=2)
+    c = q.Circuit(text)
+    p, seed = 2e-3, 5
+    shots = q.pauli_prescreen(c, 0, 64 * 64, p=p, seed=seed)["survivors"][:10]
+    K = _n_readouts(c)
+    _, res, rec = q.mps_sample_batch_traced(c, shots, p=p, seed=seed, chi_max=256, cutoff=1e-10, precision=prec,
+                                            readout_k=K)
+    pick = [int(s) for s in res["shot"]]
+    faults = sampler.draw_faults(parse(text), p=p, seed=seed, shots=pick)
+    ref = oracle_shots(text, pick, faults, seed=seed, chi_max=256, cutoff=1e-10)
+    _compare(res, rec, ref, tol, tol, allow_flip=0 if prec == 1 else 1)
+    assert res["chi_peak"].max() >= 64, res["chi_peak"]
+    assert (res["status"] >= 0).all()
