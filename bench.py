@@ -113,21 +113,25 @@ def measured_peaks():
         return {}
 
 
-# DRAM bytes (read + write) of one engine launch of the benchmark step, from the ncu launch list
-# summary under profiles/, valid only for the engine source it was taken on
-ENGINE_TRAFFIC = {"mps_cu_sha256": "a317903e6241f6ac13bb55cdba84dd3c01820400f479570f2f97f3248279e88a",
-                  "bytes_per_launch": 34.48e9 + 101.59e9}
+# DRAM bytes (read + write) per site operation (two-site update or centre move) of the engine, from one
+# ncu capture of the small case (`--case engine-prefix6`: the benchmark circuit's first 6 layers, 1,332
+# survivors, one launch, DRAM counters in one pass; summary under profiles/).  The benchmark launch is too
+# large to capture with counters, so its traffic is this figure times its site operations; valid only
+# for the engine source the capture was taken on (null otherwise).
+ENGINE_TRAFFIC = {"mps_cu_sha256": None, "bytes_per_site_op": None}
 
 
-def engine_traffic():
-    """The recorded per-launch traffic when the engine source is unchanged since the capture."""
+def engine_traffic(site_ops):
+    """Per-launch DRAM traffic scaled from the small-case capture, when the engine source is unchanged."""
     import hashlib
     path = os.path.join(HERE, "paper_2609_19116_b300", "csrc", "mps.cu")
     try:
         digest = hashlib.sha256(open(path, "rb").read()).hexdigest()
     except OSError:
         return None
-    return ENGINE_TRAFFIC["bytes_per_launch"] if digest == ENGINE_TRAFFIC["mps_cu_sha256"] else None
+    if ENGINE_TRAFFIC["mps_cu_sha256"] != digest or not ENGINE_TRAFFIC["bytes_per_site_op"]:
+        return None
+    return ENGINE_TRAFFIC["bytes_per_site_op"] * site_ops
 
 
 def fp32_alu_peak_tflops(sm_max_mhz, nsm=148):
@@ -522,7 +526,10 @@ def profiling_case(args):
     import paper_2609_19116_b300 as q
     from synth import workload_circuit
     if args.case == "engine-prefix6":
-        c = q.Circuit(workload_circuit(WORKLOAD, seed=args.seed, layers=6))
+        # the launch rule (warp per shot, 24 KB) unless QCMPS_ENGINE / QCMPS_SMEM_KB say otherwise: no
+        # calibration launches inside the captured window
+        os.environ.setdefault("QCMPS_NO_TUNE", "1")
+        c = q.Circuit(workload_circuit(WORKLOAD, seed=args.seed, prefix_layers=6))
         surv = q.pauli_prescreen(c, 0, 64 * 20000, p=args.p, seed=args.seed)["survivors"][:1332]
         q.mps_sample_batch(c, surv[:1], p=args.p, seed=args.seed, chi_max=args.chi_max, cutoff=args.cutoff)
         torch.cuda.synchronize()
@@ -531,7 +538,7 @@ def profiling_case(args):
         torch.cuda.synchronize()
         dt = time.perf_counter() - t
         print(json.dumps({"case": args.case, "shots": int(surv.numel()), "seconds": dt,
-                          "updates": int(res["n_updates"].sum()), "alg_flops": float(res["alg_flops"].sum()),
+                          "site_ops": int(res["n_updates"].sum()), "alg_flops": float(res["alg_flops"].sum()),
                           "sweeps_per_update": float(res["sweeps"].sum() / max(1, res["n_updates"].sum()))}))
     else:
         c = q.Circuit(workload_circuit("d5_49q_200l", seed=args.seed))
@@ -588,6 +595,7 @@ def main():
     kernel_ms = []
     launch = {}  # the engine's launch configuration (autotuned on the first batch)
     flops_dev = torch.zeros((), dtype=torch.float64, device="cuda")  # summed over the timed steps
+    site_ops_dev = torch.zeros((), dtype=torch.int64, device="cuda")
     last = {}
 
     def step(k, timed):
@@ -606,6 +614,9 @@ def main():
             recs = shot_buf[: surv.numel() * q.SHOT_DTYPE.itemsize].view(torch.float64)
             recs = recs.view(-1, q.SHOT_DTYPE.itemsize // 8)
             flops_dev.add_(recs[:, q.SHOT_DTYPE.fields["alg_flops"][1] // 8].sum())
+            ops_i32 = shot_buf[: surv.numel() * q.SHOT_DTYPE.itemsize].view(torch.int32).view(
+                -1, q.SHOT_DTYPE.itemsize // 4)
+            site_ops_dev.add_(ops_i32[:, q.SHOT_DTYPE.fields["n_updates"][1] // 4].sum())
         last["counts"] = counts
         last["n"] = int(surv.numel())
         return int(counts[:, 1].sum()), int(surv.numel())
@@ -724,9 +735,10 @@ def main():
                    "l2": "each step reads fresh site-tensor slots and a new shot range; working set > L2"},
         "gpu_launches": args.steps * 5,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-                     "frac": achieved / alu_peak if alu_peak else None, "traffic": engine_traffic(),
-                     "traffic_note": "DRAM read+write bytes per engine launch from one ncu capture of this "
-                                     "engine source (null when the source changed since)",
+                     "frac": achieved / alu_peak if alu_peak else None, "traffic": (engine_traffic(int(site_ops_dev)) / len(kernel_ms) if engine_traffic(1) else None),
+                     "traffic_note": "DRAM read+write bytes per engine launch: bytes per site operation from an "
+                                     "ncu capture of the 6-layer prefix case x this launch's site operations "
+                                     "(null when the engine source changed since the capture)",
                      "kernel": ("engine_kernel<float,%d> (%s, %d KB work area, autotuned)" % (
                          launch.get("threads", 0), "one warp per shot" if launch.get("threads") == 32
                          else "one CTA per shot", launch.get("kb", 0))),

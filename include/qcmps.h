@@ -183,7 +183,8 @@ typedef struct {
                                 8 r M N */
     int32_t gmem_updates;    /* two-site updates whose Jacobi matrix did not fit the engine's shared
                                 memory and was rotated in global memory (blocked Jacobi) */
-    int32_t reserved;
+    int32_t fp64_resplits;   /* QC_C64: splits redone in FP64 because the truncation cut inside a cluster
+                                of singular values that FP32 cannot tell apart */
 } qc_shot_result;
 
 /* Simulate the given shots (typically pre-screen survivors) as MPS: single-site gates in place;

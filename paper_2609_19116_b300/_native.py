@@ -50,7 +50,7 @@ class ShotResult(C.Structure):
                 ("logical_error", C.c_int32), ("chi_peak", C.c_int32), ("abort_op", C.c_int64),
                 ("fidelity", C.c_double), ("discarded", C.c_double), ("degenerate_cuts", C.c_int32),
                 ("n_updates", C.c_int32), ("sweeps", C.c_int32), ("alg_flops", C.c_double),
-                ("gmem_updates", C.c_int32), ("reserved", C.c_int32)]
+                ("gmem_updates", C.c_int32), ("fp64_resplits", C.c_int32)]
 
 
 class MpsTrace(C.Structure):

