@@ -78,12 +78,14 @@ _lib = None
 
 
 def lib():
+    """The library: the in-tree build, or the file named by QCMPS_LIB (for comparing builds)."""
     global _lib
     if _lib is None:
-        if not os.path.exists(LIB_PATH):
-            raise ImportError(f"qcmps CUDA library not built ({LIB_PATH}); run "
+        path = os.environ.get("QCMPS_LIB") or LIB_PATH
+        if not os.path.exists(path):
+            raise ImportError(f"qcmps CUDA library not built ({path}); run "
                               "`python -m paper_2609_19116_b300.build`")
-        L = C.CDLL(LIB_PATH)
+        L = C.CDLL(path)
         vp, u64, i32, sz = C.c_void_p, C.c_uint64, C.c_int32, C.c_size_t
         sig = {
             "qc_last_error": (C.c_char_p, []),

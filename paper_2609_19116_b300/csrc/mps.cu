@@ -41,6 +41,70 @@ template <typename V> __device__ __forceinline__ V cfmac(V a, V b, V c) {  // co
     return cmk<V>(fma(a.x, b.x, fma(a.y, b.y, c.x)), fma(a.x, b.y, fma(-a.y, b.x, c.y)));
 }
 
+// sum_i conj(u[i]) t[i * ts] and sum_i t[i * ts] u[i] over n terms, as two interleaved partial sums (even
+// and odd i) so that two dependent complex-FMA chains run side by side; complex64 uses the paired FP32 FMA
+// (real and imaginary parts in one 64-bit register).
+template <typename V>
+__device__ __forceinline__ V dot_conj(const V* u, const V* t, size_t ts, int n) {
+    if constexpr (sizeof(V) == 8) {
+        float2 a0 = make_float2(0.f, 0.f), a1 = a0, b0 = a0, b1 = a0;
+        int i = 0;
+        for (; i + 1 < n; i += 2) {
+            const float2 x0 = u[i], y0 = t[(size_t)i * ts], x1 = u[i + 1], y1 = t[(size_t)(i + 1) * ts];
+            a0 = __ffma2_rn(make_float2(x0.x, x0.x), y0, a0);                      // (ux tx, ux ty)
+            b0 = __ffma2_rn(make_float2(x0.y, -x0.y), make_float2(y0.y, y0.x), b0);  // (uy ty, -uy tx)
+            a1 = __ffma2_rn(make_float2(x1.x, x1.x), y1, a1);
+            b1 = __ffma2_rn(make_float2(x1.y, -x1.y), make_float2(y1.y, y1.x), b1);
+        }
+        if (i < n) {
+            const float2 x0 = u[i], y0 = t[(size_t)i * ts];
+            a0 = __ffma2_rn(make_float2(x0.x, x0.x), y0, a0);
+            b0 = __ffma2_rn(make_float2(x0.y, -x0.y), make_float2(y0.y, y0.x), b0);
+        }
+        const float2 s = __fadd2_rn(__fadd2_rn(a0, a1), __fadd2_rn(b0, b1));
+        return cmk<V>(s.x, s.y);
+    } else {
+        V a0 = cmk<V>(0, 0), a1 = a0;
+        int i = 0;
+        for (; i + 1 < n; i += 2) {
+            a0 = cfmac(u[i], t[(size_t)i * ts], a0);
+            a1 = cfmac(u[i + 1], t[(size_t)(i + 1) * ts], a1);
+        }
+        if (i < n) a0 = cfmac(u[i], t[(size_t)i * ts], a0);
+        return cadd(a0, a1);
+    }
+}
+template <typename V>
+__device__ __forceinline__ V dot_plain(const V* t, const V* u, int n) {  // sum_i t[i] u[i]
+    if constexpr (sizeof(V) == 8) {
+        float2 a0 = make_float2(0.f, 0.f), a1 = a0, b0 = a0, b1 = a0;
+        int i = 0;
+        for (; i + 1 < n; i += 2) {
+            const float2 x0 = t[i], y0 = u[i], x1 = t[i + 1], y1 = u[i + 1];
+            a0 = __ffma2_rn(make_float2(x0.x, x0.x), y0, a0);                       // (tx ux, tx uy)
+            b0 = __ffma2_rn(make_float2(-x0.y, x0.y), make_float2(y0.y, y0.x), b0);  // (-ty uy, ty ux)
+            a1 = __ffma2_rn(make_float2(x1.x, x1.x), y1, a1);
+            b1 = __ffma2_rn(make_float2(-x1.y, x1.y), make_float2(y1.y, y1.x), b1);
+        }
+        if (i < n) {
+            const float2 x0 = t[i], y0 = u[i];
+            a0 = __ffma2_rn(make_float2(x0.x, x0.x), y0, a0);
+            b0 = __ffma2_rn(make_float2(-x0.y, x0.y), make_float2(y0.y, y0.x), b0);
+        }
+        const float2 s = __fadd2_rn(__fadd2_rn(a0, a1), __fadd2_rn(b0, b1));
+        return cmk<V>(s.x, s.y);
+    } else {
+        V a0 = cmk<V>(0, 0), a1 = a0;
+        int i = 0;
+        for (; i + 1 < n; i += 2) {
+            a0 = cfma(t[i], u[i], a0);
+            a1 = cfma(t[i + 1], u[i + 1], a1);
+        }
+        if (i < n) a0 = cfma(t[i], u[i], a0);
+        return cadd(a0, a1);
+    }
+}
+
 constexpr int MAXF = 128;     // faults per shot
 constexpr int OPCH = 32;      // program ops staged per step
 
@@ -94,6 +158,7 @@ struct EngineParams {
     int sweep_cap;
     unsigned long long* phase_cycles;  // optional [8]: SM cycles per phase of the shots, summed
     int use_tc;                // CTA variants: two-site contractions of large theta on the tensor cores
+    int track_norms;           // Jacobi tracks the column norms instead of summing them every pair
     double* trace_p1;          // optional [ntasks x trace_k]: readout probabilities of each shot
     const uint64_t* trace_pos; // optional: record row of each task (the capacity re-run pass)
     int trace_k;
@@ -300,8 +365,9 @@ struct Engine {
 
     // The rotation of one pair: a <- c a - w b,  b <- conj(w) a + c b,  w = s e^{-i phi} = (wr, wi).
     template <typename RS>
-    __device__ __forceinline__ void pair_rotate(typename VecOf<RS>::T* a, typename VecOf<RS>::T* b, int rows, int gl,
-                                                int g, RS c, RS wr, RS wi) {
+    __device__ __forceinline__ void pair_rotate(typename VecOf<RS>::T* a,
+                                                typename VecOf<RS>::T* b, int rows, int gl, int g, RS c,
+                                                RS wr, RS wi) {
         using VS = typename VecOf<RS>::T;
         if constexpr (sizeof(RS) == 4) {
             const float2 cc = make_float2(c, c), nw = make_float2(-wr, -wr), ws = make_float2(wi, -wi);
@@ -357,6 +423,83 @@ struct Engine {
         return 0;
     }
 
+    // gamma = a^H b only (the column norms are tracked), same lane layout as pair_dots.
+    template <typename RS>
+    __device__ __forceinline__ void pair_gamma(const typename VecOf<RS>::T* a,
+                                               const typename VecOf<RS>::T* b, int rows, int gl, int g,
+                                               RS& gr, RS& gi) {
+        using VS = typename VecOf<RS>::T;
+        if constexpr (sizeof(RS) == 4) {
+            float2 sg = make_float2(0.f, 0.f), sh = sg;
+            for (int i = gl; i < rows; i += g) {
+                const float2 x = a[i], y = b[i];
+                sg = __ffma2_rn(x, y, sg);                            // (x.re y.re, x.im y.im)
+                sh = __ffma2_rn(x, make_float2(y.y, y.x), sh);         // (x.re y.im, x.im y.re)
+            }
+            gr = sg.x + sg.y;
+            gi = sh.x - sh.y;
+        } else {
+            for (int i = gl; i < rows; i += g) {
+                const VS x = a[i], y = b[i];
+                gr = fma(x.x, y.x, fma(x.y, y.y, gr));
+                gi = fma(x.x, y.y, fma(-x.y, y.x, gi));
+            }
+        }
+    }
+
+    // pair_step with the squared column norms tracked in na, nb: a rotation that zeroes gamma changes
+    // them exactly to alpha - t |gamma| and beta + t |gamma| (t the tangent of the angle), so only gamma
+    // is summed over the rows.  The norms are recomputed at the start of every sweep.
+    template <typename RS>
+    __device__ __forceinline__ int pair_step_n(typename VecOf<RS>::T* a, typename VecOf<RS>::T* b, int rows, int gl,
+                                               int g, bool act, RS tol, RS floor2, RS* na, RS* nb) {
+        RS gr = 0, gi = 0;
+        RS al = 0, be = 0;
+        if (act) {
+            al = *na;
+            be = *nb;
+            pair_gamma(a, b, rows, gl, g, gr, gi);
+        }
+        for (int o = g >> 1; o > 0; o >>= 1) {
+            gr += __shfl_xor_sync(0xFFFFFFFFu, gr, o);
+            gi += __shfl_xor_sync(0xFFFFFFFFu, gi, o);
+        }
+        const RS g2 = gr * gr + gi * gi;
+        if (act && g2 > tol * tol * (al * be) && g2 > (RS)0 && fmin(al, be) > floor2) {
+            const RS rg = rs_sqrt(g2);                    // 1 / |gamma|
+            const RS zeta = (be - al) * (RS)0.5 * rg;
+            const RS t = fdiv(zeta >= 0 ? (RS)1 : (RS)-1, fabs(zeta) + sqrt((RS)1 + zeta * zeta));
+            const RS c = rs_sqrt((RS)1 + t * t), sn = c * t;
+            pair_rotate(a, b, rows, gl, g, c, sn * gr * rg, -sn * gi * rg);
+            if (gl == 0) {
+                const RS tg = t * g2 * rg;  // t |gamma|
+                *na = al - tg;
+                *nb = be + tg;
+            }
+            return 1;
+        }
+        return 0;
+    }
+
+    // Squared norms of the columns of X into nrm (lane groups as in the sweeps).
+    template <typename RS>
+    __device__ void column_norms(const typename VecOf<RS>::T* X, int rows, int cols, int ld, RS* nrm) {
+        const int wid = tid_ >> 5;
+        constexpr int NW = NT / 32;
+        int G, g, grp, gl;
+        lane_groups(cols, rows, G, g, grp, gl);
+        for (int base = wid * G; base < cols; base += NW * G) {
+            const int j = base + grp;
+            RS sq = 0;
+            if (j < cols) {
+                const auto* col = X + (size_t)j * ld;
+                for (int i = gl; i < rows; i += g) sq = fma(col[i].x, col[i].x, fma(col[i].y, col[i].y, sq));
+            }
+            for (int o = g >> 1; o > 0; o >>= 1) sq += __shfl_xor_sync(0xFFFFFFFFu, sq, o);
+            if (j < cols && gl == 0) nrm[j] = sq;
+        }
+    }
+
     // Lane groups for `pairs` concurrent pairs: G groups of g = 32 / G lanes per warp (G a power of
     // two, at least 2 lanes per pair when the rows allow it), so that small matrices keep every lane
     // busy and reduce over short shuffle trees.
@@ -383,7 +526,7 @@ struct Engine {
     // their lane groups.
     template <typename RS>
     __device__ bool jacobi(typename VecOf<RS>::T* X, int rows, int cols, int ld, RS floor2, int max_sweeps = 0,
-                           int* any_rotation = nullptr) {
+                           int* any_rotation = nullptr, RS* nrm = nullptr) {
         const int wid = tid_ >> 5;
         constexpr int NW = NT / 32;
         const RS tol = jacobi_tol<RS>(rows);
@@ -393,6 +536,10 @@ struct Engine {
         const int cap = max_sweeps > 0 ? max_sweeps : P.sweep_cap;
         for (int sweep = 0; sweep < cap; ++sweep) {
             int rotated = 0;
+            if (nrm) {
+                column_norms<RS>(X, rows, cols, ld, nrm);
+                bsync<NT>();
+            }
             for (int k = 0; k < cm1; ++k) {
                 for (int base = wid * G; base < half; base += NW * G) {
                     const int pr = base + grp;
@@ -404,7 +551,11 @@ struct Engine {
                     ib -= ib >= cm1 ? cm1 : 0;
                     const int ca = sa == 0 ? 0 : 1 + ia;
                     const int cb = 1 + ib;
-                    rotated |= pair_step(X + (size_t)ca * ld, X + (size_t)cb * ld, rows, gl, g, act, tol, floor2);
+                    if (nrm)
+                        rotated |= pair_step_n(X + (size_t)ca * ld, X + (size_t)cb * ld, rows, gl, g, act, tol, floor2,
+                                               nrm + ca, nrm + cb);
+                    else
+                        rotated |= pair_step(X + (size_t)ca * ld, X + (size_t)cb * ld, rows, gl, g, act, tol, floor2);
                 }
                 bsync<NT>();
             }
@@ -906,7 +1057,7 @@ struct Engine {
         gmem_updates += in_global ? 1 : 0;
         tock(PH_CONTRACT);
         if (!(blocked ? jacobi_blocked<RS>(X, rows, cols, ld, floor2, reinterpret_cast<VS*>(S.X), bw)
-                      : jacobi<RS>(X, rows, cols, ld, floor2))) {
+                      : jacobi<RS>(X, rows, cols, ld, floor2, 0, nullptr, P.track_norms ? sig2 : nullptr))) {
             status = QC_ENOCONV;
             release_big(locked);
             return SPLIT_FAIL;
@@ -948,9 +1099,7 @@ struct Engine {
             }
             for (int e = tid_; e < r * n; e += NT) {
                 const int k = e / n, j = e - k * n;
-                const VS* u = X + (size_t)perm[k] * ld;
-                VS acc = cmk<VS>(0, 0);
-                for (int i = 0; i < m; ++i) acc = cfmac(u[i], T[(size_t)i * n + j], acc);
+                const VS acc = dot_conj(X + (size_t)perm[k] * ld, T + j, (size_t)n, m);
                 Bs[e] = cmk<V>(acc.x * scale, acc.y * scale);
             }
         } else if (!xt && !right) {
@@ -962,9 +1111,7 @@ struct Engine {
             }
             for (int e = tid_; e < m * r; e += NT) {
                 const int i = e / r, k = e - i * r;
-                const VS* u = X + (size_t)perm[k] * ld;
-                VS acc = cmk<VS>(0, 0);
-                for (int j = 0; j < n; ++j) acc = cfma(T[(size_t)i * n + j], u[j], acc);
+                const VS acc = dot_plain(T + (size_t)i * n, X + (size_t)perm[k] * ld, n);
                 As[e] = cmk<V>(acc.x * scale, acc.y * scale);
             }
         } else if (xt) {
@@ -978,9 +1125,7 @@ struct Engine {
             }
             for (int e = tid_; e < r * n; e += NT) {
                 const int k = e / n, j = e - k * n;
-                const VS* u = X + (size_t)perm[k] * ld;
-                VS acc = cmk<VS>(0, 0);
-                for (int i = 0; i < m; ++i) acc = cfmac(u[i], T[(size_t)i * n + j], acc);
+                const VS acc = dot_conj(X + (size_t)perm[k] * ld, T + j, (size_t)n, m);
                 const RS sgk = sig2[perm[k]];
                 const RS inv = sgk > (RS)0 ? (RS)1 / sqrt(sgk) : (RS)0;
                 Bs[e] = cmk<V>(acc.x * inv, acc.y * inv);
@@ -996,9 +1141,7 @@ struct Engine {
             }
             for (int e = tid_; e < m * r; e += NT) {
                 const int i = e / r, k = e - i * r;
-                const VS* u = X + (size_t)perm[k] * ld;
-                VS acc = cmk<VS>(0, 0);
-                for (int j = 0; j < n; ++j) acc = cfma(T[(size_t)i * n + j], u[j], acc);
+                const VS acc = dot_plain(T + (size_t)i * n, X + (size_t)perm[k] * ld, n);
                 const RS sgk = sig2[perm[k]];
                 const RS inv = sgk > (RS)0 ? (RS)1 / sqrt(sgk) : (RS)0;
                 As[e] = cmk<V>(acc.x * inv, acc.y * inv);
@@ -1072,12 +1215,20 @@ struct Engine {
                 }
                 bsync<NT>();
                 part = 0;
-                for (int t = tid_; t < rows; t += NT) {  // x -= sum_i h_i q_i
-                    V acc = x[t];
-                    for (int i = 0; i < k; ++i) {
+                for (int t = tid_; t < rows; t += NT) {  // x -= sum_i h_i q_i (two partial sums)
+                    V acc = x[t], acc1 = cmk<V>(0, 0);
+                    int i = 0;
+                    for (; i + 1 < k; i += 2) {
+                        const V h = hb[i], u = X[(size_t)perm[i] * ld + t];
+                        const V h1 = hb[i + 1], u1 = X[(size_t)perm[i + 1] * ld + t];
+                        acc = cmk<V>(acc.x - (h.x * u.x - h.y * u.y), acc.y - (h.x * u.y + h.y * u.x));
+                        acc1 = cmk<V>(acc1.x + (h1.x * u1.x - h1.y * u1.y), acc1.y + (h1.x * u1.y + h1.y * u1.x));
+                    }
+                    if (i < k) {
                         const V h = hb[i], u = X[(size_t)perm[i] * ld + t];
                         acc = cmk<V>(acc.x - (h.x * u.x - h.y * u.y), acc.y - (h.x * u.y + h.y * u.x));
                     }
+                    acc = cmk<V>(acc.x - acc1.x, acc.y - acc1.y);
                     x[t] = acc;
                     part = fma(acc.x, acc.x, fma(acc.y, acc.y, part));
                 }
@@ -1858,11 +2009,13 @@ static uint64_t scratch_elems(int chi, int ref_chi, size_t sizeR, size_t sizeV) 
     return base;
 }
 
-// Capacity bucket of the first pass: the smallest power of two >= max(64, 2 x the reference's chi_peak),
-// at most the full capacity chi (QCMPS_CHI_ALLOC overrides it for tests and tuning).
+// Capacity bucket of the first pass: 64 when the reference's chi_peak is at most 64 (the warp variant's
+// design size: theta at most 128 x 128; shots that outgrow it go to the re-run pass, which runs one CTA
+// per shot), otherwise the smallest power of two >= 2 x the reference's chi_peak; at most the full
+// capacity chi (QCMPS_CHI_ALLOC overrides it for tests and tuning).
 static int bucket_chi(int ref_chi_peak, int chi) {
     int chi_alloc = 64;
-    while (chi_alloc < 2 * ref_chi_peak) chi_alloc *= 2;
+    while (ref_chi_peak > 64 && chi_alloc < 2 * ref_chi_peak) chi_alloc *= 2;
     chi_alloc = std::min(chi_alloc, chi);
     if (const char* ca = getenv("QCMPS_CHI_ALLOC")) chi_alloc = std::max(1, std::min(chi, atoi(ca)));
     return chi_alloc;
@@ -2148,6 +2301,7 @@ static qc_status run_engine(CircuitImpl& c, qc_noise noise, const uint64_t* shot
     P.precision = prm.precision;
     P.wmax = wmax;
     P.sweep_cap = sizeof(R) == 4 ? 40 : 60;  // the noiseless reference run always keeps the default
+    P.track_norms = getenv("QCMPS_NO_NORM_TRACKING") ? 0 : 1;
     {
         int center = 0;
         for (const MpsOp& o : c.mps) {
