@@ -51,8 +51,9 @@ def parse_args():
                     help="skip the subset-sampling leg (exactly k faults, k = 0..4, chi_max 1024)")
     ap.add_argument("--no-legs", action="store_true",
                     help="skip the other configurations (17-qubit complex128, 1e8-shot pre-screen, chi_max rows)")
-    ap.add_argument("--case", default=None, choices=["engine-prefix6", "prescreen-1e7"],
+    ap.add_argument("--case", default=None, choices=["engine-prefix6", "engine-b128", "prescreen-1e7"],
                     help="run one small profiling case once and print its timing (for ncu captures)")
+    ap.add_argument("--case-shots", type=int, default=1332, help="survivors of the engine profiling cases")
     return ap.parse_args()
 
 
@@ -519,19 +520,26 @@ def chi_rows_leg(q, circ, args, chis=(64, 128), survivors=2048):
 # ---- the GPU arm ------------------------------------------------------------------------------
 def profiling_case(args):
     """Small, self-contained cases for ncu: the MPS engine on the 6-layer prefix of the 49-qubit
-    workload with 1,332 survivors (every shot slot of one launch busy), or the pre-screen on 1e7
-    shots of the 200-layer circuit."""
+    workload (1,332 survivors fill every warp slot of one launch), the engine on the 2-layer prefix of
+    the large-bond workload (one CTA per shot), or the pre-screen on 1e7 shots of the 200-layer
+    circuit."""
     import numpy as np
     import torch
     import paper_2609_19116_b300 as q
     from synth import workload_circuit
-    if args.case == "engine-prefix6":
-        # the launch rule (warp per shot, 24 KB) unless QCMPS_ENGINE / QCMPS_SMEM_KB say otherwise: no
-        # calibration launches inside the captured window
+    if args.case in ("engine-prefix6", "engine-b128"):
+        # the launch rule (warp per shot, 24 KB, or one CTA per shot for the large-bond circuit) unless
+        # QCMPS_ENGINE / QCMPS_SMEM_KB say otherwise: no calibration launches inside the captured window
         os.environ.setdefault("QCMPS_NO_TUNE", "1")
-        c = q.Circuit(workload_circuit(WORKLOAD, seed=args.seed, prefix_layers=6))
-        surv = q.pauli_prescreen(c, 0, 64 * 20000, p=args.p, seed=args.seed)["survivors"][:1332]
-        q.mps_sample_batch(c, surv[:1], p=args.p, seed=args.seed, chi_max=args.chi_max, cutoff=args.cutoff)
+        if args.case == "engine-prefix6":
+            c = q.Circuit(workload_circuit(WORKLOAD, seed=args.seed, prefix_layers=6))
+        else:
+            c = q.Circuit(workload_circuit("d5_49q_60l_b128", seed=args.seed, prefix_layers=2))
+        surv = q.pauli_prescreen(c, 0, 64 * 20000, p=args.p, seed=args.seed)["survivors"][:args.case_shots]
+        # the noiseless reference run alone (an empty batch): the engine launches are then the reference,
+        # the first pass of the batch (the one to capture: ncu -k regex:engine_kernel -s 1 -c 1) and the
+        # re-run of shots that outgrew the capacity bucket, if any
+        q.mps_sample_batch(c, surv[:0], p=args.p, seed=args.seed, chi_max=args.chi_max, cutoff=args.cutoff)
         torch.cuda.synchronize()
         t = time.perf_counter()
         counts, res = q.mps_sample_batch(c, surv, p=args.p, seed=args.seed, chi_max=args.chi_max, cutoff=args.cutoff)

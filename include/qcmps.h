@@ -285,7 +285,8 @@ typedef struct {
  * of different jobs overlap on the device (each batch holds the shots of one job; inside it a
  * finished shot slot is back-filled with the next shot).  A chunk is launched only while its
  * footprint (slots x bytes of one slot of the capacity bucket the engine allocates) fits the
- * budget next to the chunks in flight.  Chunks go to the job with the smallest remaining work
+ * budget next to the chunks in flight (the re-run of a chunk's shots that outgrew the bucket, at full
+ * capacity, is not charged: it can exceed the budget by its shots x one full-capacity slot).  Chunks go to the job with the smallest remaining work
  * divided by 1 + age/1 s (age since submission); jobs older than 2 s go first, oldest first.
  * *out is owned by the library; release with mps_serve_destroy. */
 qc_status mps_serve_create(const qc_serve_cfg* cfg, qc_server** out);

@@ -2270,8 +2270,8 @@ static qc_status run_engine(CircuitImpl& c, qc_noise noise, const uint64_t* shot
     const uint64_t x_full = (uint64_t)(2 * chi + 1) * (2 * chi);
     const uint64_t over_full = (uint64_t)chi * chi * 3;
     const uint64_t xg_elems = std::max(x_full, over_full);
-    const uint64_t sg_elems = ((uint64_t)(2 * chi) * (sizeof(R) + sizeof(int)) + sizeof(V) - 1) / sizeof(V) + 2;
-    const uint64_t scratch_stride = xg_elems + (uint64_t)(2 * chi) * (2 * chi) + sg_elems;
+    // the same split scratch as the shots' slots (scratch_elems), including the room of an FP64 re-split
+    const uint64_t scratch_stride = scratch_elems(chi, chi, sizeof(R), sizeof(V));
 
     int dev = 0, nsm = 0;
     QC_CUDA(cudaGetDevice(&dev));
@@ -2474,9 +2474,11 @@ static qc_status run_engine(CircuitImpl& c, qc_noise noise, const uint64_t* shot
         if (e != cudaSuccess) out = cuda_fail(e, "second pass");
         EngineParams<R> P2 = P;
         P2.trace_pos = pos2;
+        // the re-run holds only the shots that outgrew the bucket: all of them run at once (its slots
+        // are larger than the first pass's, so a caller's slot limit sized for those is not applied)
         if (out == QC_OK)
             out = run_pass<R, NT_BIG>(c, P2, L, ref->state, ref->cap, ref->off, *ref, shots2, redo.size(), counts_dev,
-                                      res2, s, max_slots, nsm, false, pick(P2, L, ref->cap, ref->off, redo.size(), false));
+                                      res2, s, 0, nsm, false, pick(P2, L, ref->cap, ref->off, redo.size(), false));
         if (out == QC_OK && per_shot) {
             std::vector<qc_shot_result> h2(redo.size());
             e = cudaMemcpyAsync(h2.data(), res2, h2.size() * sizeof(qc_shot_result), cudaMemcpyDeviceToHost, s);
