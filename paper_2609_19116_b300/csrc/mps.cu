@@ -733,10 +733,14 @@ struct Engine {
                 // FP32: the Jacobi stops at |a^H b| <= 4 eps sqrt(rows) |a||b|, so squared norms closer
                 // than 32 eps sqrt(rows) relative are not told apart); a dropped value at the numerical
                 // floor is not a cluster member
+                // FP32 also needs the dropped value to carry more than the cutoff's share of the weight
+                // (a cut set by chi_max): a cut the cutoff makes among tiny near-equal values at the
+                // FP32 noise level drops at most cutoff x total whichever of them it keeps
                 if (r < cols) {
                     const double a2 = (double)sig2[perm[r - 1]], b2 = (double)sig2[perm[r]];
                     const double rel = sizeof(RS) == 8 ? 2e-8 + 1e-16 : 32.0 * FLT_EPSILON * sqrt((double)rows);
-                    dg = b2 > (double)floor2 && a2 <= b2 * (1.0 + rel);
+                    const double sig = sizeof(RS) == 8 ? (double)floor2 : fmax((double)floor2, P.cutoff * tot);
+                    dg = b2 > sig && a2 <= b2 * (1.0 + rel);
                 }
                 S.red[40] = tot > 0 ? dropped / tot : 0.0;
                 S.red[41] = kept > 0 ? 1.0 / sqrt(kept) : 0.0;
@@ -1078,12 +1082,19 @@ struct Engine {
             release_big(locked);
             return SPLIT_FAIL;
         }
+        // the kept singular values, once per column: sig2[j] <- sqrt(sig2[j])
+        for (int k = tid_; k < r; k += NT) {
+            const int j = perm[k];
+            const RS sg = sig2[j];
+            sig2[j] = sg > (RS)0 ? sqrt(sg) : (RS)0;
+        }
+        bsync<NT>();
         // normalise the kept columns to unit length (the orthonormal factor)
         for (int e = tid_; e < r * rows; e += NT) {
             const int k = e / rows, i = e - k * rows;
             const int j = perm[k];
-            const RS sg = sig2[j];
-            const RS inv = sg > (RS)0 ? (RS)1 / sqrt(sg) : (RS)0;
+            const RS sv = sig2[j];
+            const RS inv = sv > (RS)0 ? fdiv((RS)1, sv) : (RS)0;
             VS* col = X + (size_t)j * ld;
             col[i] = cmk<VS>(col[i].x * inv, col[i].y * inv);
         }
@@ -1119,15 +1130,15 @@ struct Engine {
             // A[q+1] = V^H = S^-1 U^H theta' (r, 2, cr)
             for (int e = tid_; e < m * r; e += NT) {
                 const int i = e / r, k = e - i * r;
-                const RS f = scale * sqrt(sig2[perm[k]]);
+                const RS f = scale * sig2[perm[k]];
                 const VS u = X[(size_t)perm[k] * ld + i];
                 As[e] = cmk<V>(u.x * f, u.y * f);
             }
             for (int e = tid_; e < r * n; e += NT) {
                 const int k = e / n, j = e - k * n;
                 const VS acc = dot_conj(X + (size_t)perm[k] * ld, T + j, (size_t)n, m);
-                const RS sgk = sig2[perm[k]];
-                const RS inv = sgk > (RS)0 ? (RS)1 / sqrt(sgk) : (RS)0;
+                const RS svk = sig2[perm[k]];
+                const RS inv = svk > (RS)0 ? fdiv((RS)1, svk) : (RS)0;
                 Bs[e] = cmk<V>(acc.x * inv, acc.y * inv);
             }
         } else {
@@ -1135,15 +1146,15 @@ struct Engine {
             // A[q] = V' = theta' U' S^-1 (cl, 2, r);  A[q+1] = scale * S U'^H (r, 2, cr)
             for (int e = tid_; e < r * n; e += NT) {
                 const int k = e / n, j = e - k * n;
-                const RS f = scale * sqrt(sig2[perm[k]]);
+                const RS f = scale * sig2[perm[k]];
                 const VS u = X[(size_t)perm[k] * ld + j];
                 Bs[e] = cmk<V>(u.x * f, -u.y * f);
             }
             for (int e = tid_; e < m * r; e += NT) {
                 const int i = e / r, k = e - i * r;
                 const VS acc = dot_plain(T + (size_t)i * n, X + (size_t)perm[k] * ld, n);
-                const RS sgk = sig2[perm[k]];
-                const RS inv = sgk > (RS)0 ? (RS)1 / sqrt(sgk) : (RS)0;
+                const RS svk = sig2[perm[k]];
+                const RS inv = svk > (RS)0 ? fdiv((RS)1, svk) : (RS)0;
                 As[e] = cmk<V>(acc.x * inv, acc.y * inv);
             }
         }
@@ -1178,40 +1189,43 @@ struct Engine {
             for (int i = tid_; i < rows; i += NT) part = fma(x[i].x, x[i].x, fma(x[i].y, x[i].y, part));
             R nold = sum_r(part), nnow = nold;
             for (int pass = 0; pass < 4 && k > 0; ++pass) {
-                for (int i = tid_; i < k; i += NT) {  // h_i = <q_i, x>
-                    const V* qi = X + (size_t)perm[i] * ld;
-                    V h;
-                    if constexpr (sizeof(R) == 4) {  // paired FP32 FMAs, as in the Jacobi
-                        float2 s1 = make_float2(0.f, 0.f), s2 = s1, s3 = s1, s4 = s1;
-                        int t = 0;
-                        for (; t + 1 < rows; t += 2) {
-                            const float2 u0 = qi[t], x0 = x[t], u1 = qi[t + 1], x1 = x[t + 1];
-                            s1 = __ffma2_rn(u0, x0, s1);                          // (q.re x.re, q.im x.im)
-                            s2 = __ffma2_rn(u0, make_float2(x0.y, x0.x), s2);     // (q.re x.im, q.im x.re)
-                            s3 = __ffma2_rn(u1, x1, s3);
-                            s4 = __ffma2_rn(u1, make_float2(x1.y, x1.x), s4);
+                {  // h_i = <q_i, x>: the k dot products spread over lane groups (short chains)
+                    const int wid = tid_ >> 5;
+                    constexpr int NW = NT / 32;
+                    int G, g, grp, gl;
+                    lane_groups(k, rows, G, g, grp, gl);
+                    for (int base = wid * G; base < k; base += NW * G) {
+                        const int i = base + grp;
+                        const bool act = i < k;
+                        const V* qi = X + (size_t)perm[act ? i : 0] * ld;
+                        R hr = 0, hi = 0;
+                        if (act) {
+                            if constexpr (sizeof(R) == 4) {  // paired FP32 FMAs, as in the Jacobi
+                                float2 s1 = make_float2(0.f, 0.f), s2 = s1;
+                                for (int t = gl; t < rows; t += g) {
+                                    const float2 u0 = qi[t], x0 = x[t];
+                                    s1 = __ffma2_rn(u0, x0, s1);                          // (q.re x.re, q.im x.im)
+                                    s2 = __ffma2_rn(u0, make_float2(x0.y, x0.x), s2);     // (q.re x.im, q.im x.re)
+                                }
+                                hr = s1.x + s1.y;
+                                hi = s2.x - s2.y;
+                            } else {
+                                for (int t = gl; t < rows; t += g) {
+                                    hr = fma(qi[t].x, x[t].x, fma(qi[t].y, x[t].y, hr));
+                                    hi = fma(qi[t].x, x[t].y, fma(-qi[t].y, x[t].x, hi));
+                                }
+                            }
                         }
-                        if (t < rows) {
-                            const float2 u0 = qi[t], x0 = x[t];
-                            s1 = __ffma2_rn(u0, x0, s1);
-                            s2 = __ffma2_rn(u0, make_float2(x0.y, x0.x), s2);
+                        for (int o = g >> 1; o > 0; o >>= 1) {
+                            hr += __shfl_xor_sync(0xFFFFFFFFu, hr, o);
+                            hi += __shfl_xor_sync(0xFFFFFFFFu, hi, o);
                         }
-                        s1 = __fadd2_rn(s1, s3);
-                        s2 = __fadd2_rn(s2, s4);
-                        h = cmk<V>(s1.x + s1.y, s2.x - s2.y);
-                    } else {
-                        V h0 = cmk<V>(0, 0), h1 = cmk<V>(0, 0);
-                        int t = 0;
-                        for (; t + 1 < rows; t += 2) {
-                            h0 = cfmac(qi[t], x[t], h0);
-                            h1 = cfmac(qi[t + 1], x[t + 1], h1);
+                        if (act && gl == 0) {
+                            hb[i] = cmk<V>(hr, hi);
+                            V& rr = Rm[(size_t)i * cols + j];
+                            rr = cmk<V>(rr.x + hr, rr.y + hi);
                         }
-                        if (t < rows) h0 = cfmac(qi[t], x[t], h0);
-                        h = cmk<V>(h0.x + h1.x, h0.y + h1.y);
                     }
-                    hb[i] = h;
-                    V& rr = Rm[(size_t)i * cols + j];
-                    rr = cmk<V>(rr.x + h.x, rr.y + h.y);
                 }
                 bsync<NT>();
                 part = 0;
@@ -2104,7 +2118,7 @@ static qc_status run_pass(CircuitImpl& c, EngineParams<R> P, const SlotLayout& L
     // resident on an SM gets its 128 tensor-memory columns (512 per SM) without waiting
     {
         const char* tcv = getenv("QCMPS_TC");
-        P.use_tc = (sizeof(R) == 4 && variant >= 128 && per_sm * 128 <= 512 && tcv && atoi(tcv) == 1) ? 1 : 0;
+        P.use_tc = (sizeof(R) == 4 && variant >= 128 && per_sm * 128 <= 512 && !(tcv && atoi(tcv) == 0)) ? 1 : 0;
     }
     uint64_t ctas = std::min<uint64_t>((nshots + engines - 1) / engines, (uint64_t)per_sm * nsm);
     if (max_slots > 0) ctas = std::min<uint64_t>(ctas, std::max<uint64_t>(1, (uint64_t)max_slots / engines));
@@ -2153,8 +2167,8 @@ static qc_status run_pass(CircuitImpl& c, EngineParams<R> P, const SlotLayout& L
 // pass of a circuit whose noiseless run stays at bond 64) when the batch fills the SMs or shares the GPU
 // with other batches; otherwise one CTA per shot -- 128 threads with 72 KB when sharing the GPU (it finds
 // room beside other batches' warps), else 512 threads with 200 KB (the lowest latency per shot).  The
-// re-run pass of shots that outgrew the capacity bucket is never small: in one warp it would run 256-wide
-// or larger splits.
+// re-run pass of shots that outgrew the capacity bucket always takes the 512-thread CTA: its shots have
+// large theta, and in smaller engines they would hold their job for a long time.
 static LaunchCfg rule_cfg(bool small, uint64_t nshots, int nsm, bool shared_gpu, int nt_big) {
     if (small && (nshots > (uint64_t)nsm || shared_gpu)) return LaunchCfg{32, 24, 1, 0};
     if (shared_gpu) return LaunchCfg{128, 72, 1, 0};
@@ -2408,7 +2422,8 @@ static qc_status run_engine(CircuitImpl& c, qc_noise noise, const uint64_t* shot
     auto pick = [&](const EngineParams<R>& Pp, const SlotLayout& Lp, const int* cp, const uint64_t* op,
                     uint64_t n, bool first) {
         const bool small = first && ref->chi_peak <= 64;
-        LaunchCfg cf = rule_cfg(small, n, nsm, shared_gpu, NT_BIG);
+        // the re-run pass (few shots, large theta) takes the largest CTA whether or not the GPU is shared
+        LaunchCfg cf = first ? rule_cfg(small, n, nsm, shared_gpu, NT_BIG) : LaunchCfg{NT_BIG, 200, 1, 0};
         if (env_cfg(cf, NT_BIG)) return cf;
         if (first && !shared_gpu && n >= 2ull * (uint64_t)nsm && !getenv("QCMPS_NO_TUNE"))
             cf = tuned_cfg<R, NT_BIG>(c, Pp, Lp, ref->state, cp, op, *ref, shots_dev, n, s, nsm, dev, small, cf);
