@@ -51,7 +51,7 @@ def parse_args():
                     help="skip the subset-sampling leg (exactly k faults, k = 0..4, chi_max 1024)")
     ap.add_argument("--no-legs", action="store_true",
                     help="skip the other configurations (17-qubit complex128, 1e8-shot pre-screen, chi_max rows)")
-    ap.add_argument("--case", default=None, choices=["engine-prefix6", "engine-b128", "prescreen-1e7"],
+    ap.add_argument("--case", default=None, choices=["engine-prefix6", "engine-60l", "engine-b128", "prescreen-1e7"],
                     help="run one small profiling case once and print its timing (for ncu captures)")
     ap.add_argument("--case-shots", type=int, default=1332, help="survivors of the engine profiling cases")
     return ap.parse_args()
@@ -520,19 +520,22 @@ def chi_rows_leg(q, circ, args, chis=(64, 128), survivors=2048):
 # ---- the GPU arm ------------------------------------------------------------------------------
 def profiling_case(args):
     """Small, self-contained cases for ncu: the MPS engine on the 6-layer prefix of the 49-qubit
-    workload (1,332 survivors fill every warp slot of one launch), the engine on the 2-layer prefix of
-    the large-bond workload (one CTA per shot), or the pre-screen on 1e7 shots of the 200-layer
+    workload (1,332 survivors fill every warp slot of one launch), the engine on the whole 60-layer
+    workload (the same 1,332 slots, the benchmark's launch on fewer shots), the engine on the 2-layer
+    prefix of the large-bond workload (one CTA per shot), or the pre-screen on 1e7 shots of the 200-layer
     circuit."""
     import numpy as np
     import torch
     import paper_2609_19116_b300 as q
     from synth import workload_circuit
-    if args.case in ("engine-prefix6", "engine-b128"):
+    if args.case in ("engine-prefix6", "engine-60l", "engine-b128"):
         # the launch rule (warp per shot, 24 KB, or one CTA per shot for the large-bond circuit) unless
         # QCMPS_ENGINE / QCMPS_SMEM_KB say otherwise: no calibration launches inside the captured window
         os.environ.setdefault("QCMPS_NO_TUNE", "1")
         if args.case == "engine-prefix6":
             c = q.Circuit(workload_circuit(WORKLOAD, seed=args.seed, prefix_layers=6))
+        elif args.case == "engine-60l":
+            c = q.Circuit(workload_circuit(WORKLOAD, seed=args.seed))
         else:
             c = q.Circuit(workload_circuit("d5_49q_60l_b128", seed=args.seed, prefix_layers=2))
         surv = q.pauli_prescreen(c, 0, 64 * 20000, p=args.p, seed=args.seed)["survivors"][:args.case_shots]

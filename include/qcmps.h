@@ -155,7 +155,7 @@ qc_status pauli_prescreen_noalloc(const qc_circuit* circuit, qc_noise noise, uin
 enum { QC_C64 = 0, QC_C128 = 1 };
 
 typedef struct {
-    int32_t chi_max;     /* bond dimension cap */
+    int32_t chi_max;     /* bond dimension cap, 1 .. 1024 */
     double cutoff;       /* discarded-weight cutoff of the truncation rule */
     int32_t precision;   /* QC_C64: complex64 site tensors and SVD, FP64 probabilities and
                             discarded weight; QC_C128: complex128 throughout */
@@ -285,8 +285,10 @@ typedef struct {
  * of different jobs overlap on the device (each batch holds the shots of one job; inside it a
  * finished shot slot is back-filled with the next shot).  A chunk is launched only while its
  * footprint (slots x bytes of one slot of the capacity bucket the engine allocates) fits the
- * budget next to the chunks in flight (the re-run of a chunk's shots that outgrew the bucket, at full
- * capacity, is not charged: it can exceed the budget by its shots x one full-capacity slot).  Chunks go to the job with the smallest remaining work
+ * budget next to the chunks in flight; a chunk granted fewer slots than it has shots shrinks to two
+ * shots per slot (the rest of the job waits for memory).  The re-run of a chunk's shots that outgrew
+ * the bucket, at full capacity, is not charged: it can exceed the budget by its shots x one
+ * full-capacity slot.  Chunks go to the job with the smallest remaining work
  * divided by 1 + age/1 s (age since submission); jobs older than 2 s go first, oldest first.
  * *out is owned by the library; release with mps_serve_destroy. */
 qc_status mps_serve_create(const qc_serve_cfg* cfg, qc_server** out);

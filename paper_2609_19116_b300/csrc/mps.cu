@@ -106,6 +106,10 @@ __device__ __forceinline__ V dot_plain(const V* t, const V* u, int n) {  // sum_
 }
 
 constexpr int MAXF = 128;     // faults per shot
+// Internal per-shot status: the shot met a truncation that cuts inside a cluster of singular values and
+// runs in a one-warp engine, which has no FP64 split; it is re-run by a CTA engine that redoes such splits
+// in FP64.  Never reported to the caller.
+constexpr int QC_INTERNAL_FP64_RERUN = -100;
 constexpr int OPCH = 32;      // program ops staged per step
 
 template <typename R>
@@ -227,6 +231,17 @@ __device__ __forceinline__ float rs_sqrt(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double rs_sqrt(double x) { return 1.0 / sqrt(x); }
 __device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
 __device__ __forceinline__ double fdiv(double a, double b) { return a / b; }
+
+// The engine's dynamic shared memory.  A pointer into it, rebased with as_smem, is one the compiler knows
+// to be a shared-memory address: loads and stores through it are 32-bit-addressed LDS / STS instead of
+// generic 64-bit accesses (the work areas are reached through pointers that may also point to global
+// scratch, which makes them generic).
+extern __shared__ __align__(16) unsigned char qc_dsmem[];
+template <typename T>
+__device__ __forceinline__ T* as_smem(T* p) {
+    const size_t off = __cvta_generic_to_shared(p) - __cvta_generic_to_shared(qc_dsmem);
+    return reinterpret_cast<T*>(qc_dsmem + off);
+}
 
 template <typename R, int NT>
 struct Engine {
@@ -501,15 +516,14 @@ struct Engine {
     }
 
     // Lane groups for `pairs` concurrent pairs: G groups of g = 32 / G lanes per warp (G a power of
-    // two, at least 2 lanes per pair when the rows allow it), so that small matrices keep every lane
-    // busy and reduce over short shuffle trees.
+    // two, up to one lane per pair), so that small matrices keep every lane busy and reduce over short
+    // shuffle trees.
     __device__ __forceinline__ void lane_groups(int pairs, int rows, int& G, int& g, int& grp, int& gl) const {
         constexpr int NW = NT / 32;
         const int lane = tid_ & 31;
         const int ppw = (pairs + NW - 1) / NW;
         G = 1;
         while (G < ppw && G < 32) G <<= 1;
-        while (G > 1 && 32 / G < 2 && rows > 32 / G) G >>= 1;
         g = 32 / G;
         grp = lane / g;
         gl = lane - grp * g;
@@ -523,10 +537,12 @@ struct Engine {
 
     // ---- one-sided Jacobi on the columns of X (rows x cols, cols even, leading dimension ld) -----
     // Round-robin ordering: cols-1 rounds of cols/2 disjoint column pairs, spread over the warps and
-    // their lane groups.
+    // their lane groups.  In the working precision X is always in shared memory (the split stages a
+    // matrix that lives in global memory block by block), so the loops take shared-memory addressing.
     template <typename RS>
     __device__ bool jacobi(typename VecOf<RS>::T* X, int rows, int cols, int ld, RS floor2, int max_sweeps = 0,
                            int* any_rotation = nullptr, RS* nrm = nullptr) {
+        if constexpr (sizeof(RS) == sizeof(R)) X = as_smem(X);
         const int wid = tid_ >> 5;
         constexpr int NW = NT / 32;
         const RS tol = jacobi_tol<RS>(rows);
@@ -572,7 +588,7 @@ struct Engine {
     // (i + k) mod n_l of the larger (n_l columns): each round is a set of disjoint pairs, and n_l
     // rounds visit all ni x nj pairs once.  Returns 1 when this thread's group rotated.
     template <typename RS>
-    __device__ int cross_pass(typename VecOf<RS>::T* X, int rows, int ni, int nj, int ld, RS floor2) {
+    __device__ __forceinline__ int cross_pass(typename VecOf<RS>::T* X, int rows, int ni, int nj, int ld, RS floor2) {
         const int wid = tid_ >> 5;
         constexpr int NW = NT / 32;
         const RS tol = jacobi_tol<RS>(rows);
@@ -598,14 +614,16 @@ struct Engine {
     }
 
     // ---- block Jacobi for an X that lives in global memory ----------------------------------------
-    // The columns are cut into blocks of bw (even) that fit twice into the shared work area W.  One
-    // outer sweep visits every column pair exactly once, as one cyclic sweep of the plain Jacobi does
-    // in another order: the blocks are paired round-robin; each pair is staged into shared memory once,
-    // in the first round each block's internal pairs get one round-robin pass, and in every round the
-    // staged pair's cross pairs are rotated; then the pair is written back.
+    // The columns are cut into blocks of bw (even, or 1 when only two columns fit) that fit twice into
+    // the shared work area W.  One outer sweep visits every column pair exactly once, as one cyclic
+    // sweep of the plain Jacobi does in another order: the blocks are paired round-robin; each pair is
+    // staged into shared memory once, in the first round each block's internal pairs get one
+    // round-robin pass, and in every round the staged pair's cross pairs are rotated; then the pair is
+    // written back.
     template <typename RS>
     __device__ bool jacobi_blocked(typename VecOf<RS>::T* X, int rows, int cols, int ld, RS floor2,
                                    typename VecOf<RS>::T* W, int bw) {
+        W = as_smem(W);
         const int lw = rows + 1;
         const int nb = (cols + bw - 1) / bw;
         const int nbp = nb + (nb & 1);  // an even number of blocks (the last may be a dummy)
@@ -790,8 +808,13 @@ struct Engine {
         if (tid_ == 0) { reset_pend(q); reset_pend(q + 1); }
         if constexpr (sizeof(R) == 4) {
             if (split<float>(q, right) == SPLIT_REDO_FP64) {
-                ++resplits;
-                split<double>(q, right);
+                if constexpr (NT == 32) {
+                    // the warp engine stays lean (no FP64 split in its code): the shot is re-run by a CTA
+                    status = QC_INTERNAL_FP64_RERUN;
+                } else {
+                    ++resplits;
+                    split<double>(q, right);
+                }
             }
         } else {
             split<double>(q, right);
@@ -1055,9 +1078,19 @@ struct Engine {
         const RS floor2 = fl * fl * (RS)frod;
         // the blocked Jacobi stages column blocks in the engine's shared work area
         const uint32_t w_cap = (uint32_t)((uint64_t)P.x_smem * sizeof(V) / sizeof(VS));
-        const int bw = (int)(w_cap / (2 * (uint32_t)(rows + 1))) & ~1;  // even: every block pairs up
+        // blocks of bw columns, two staged at a time: even (every block pairs up inside) unless only two
+        // single columns fit, where the blocked sweep is the plain round-robin one staged pair by pair
+        int bw = (int)(w_cap / (2 * (uint32_t)(rows + 1)));
+        if (bw >= 2) bw &= ~1;
         const bool in_global = promoted || (void*)X == (void*)xg;
-        const bool blocked = in_global && bw >= 2 && bw * 2 < cols;
+        // an X in global memory always goes through the blocked Jacobi (staged in shared memory), in the
+        // working precision the only one there is; the FP64 re-split may run the plain one on global memory
+        const bool blocked = in_global && bw >= 1;
+        if (in_global && !blocked && !promoted) {
+            status = QC_ECAPACITY;  // two columns of X do not fit the work area
+            release_big(locked);
+            return SPLIT_FAIL;
+        }
         gmem_updates += in_global ? 1 : 0;
         tock(PH_CONTRACT);
         if (!(blocked ? jacobi_blocked<RS>(X, rows, cols, ld, floor2, reinterpret_cast<VS*>(S.X), bw)
@@ -1284,9 +1317,12 @@ struct Engine {
         const uint64_t other = right ? (uint64_t)cm * n : (uint64_t)m * cm;
         const uint64_t hw = (uint64_t)cm + ((uint64_t)cm * sizeof(int) + sizeof(V) - 1) / sizeof(V);
         const bool fast = (uint64_t)ld * cm + (uint64_t)cm * cm + other + hw <= P.x_smem;
-        V* X = fast ? S.X : xg;
-        V* Rm = X + (size_t)ld * cm;                  // R, row-major: kept index x cm
-        V* O = fast ? Rm + (size_t)cm * cm : nullptr;  // staged copy of the other tensor
+        // the Gram-Schmidt matrix stays in shared memory whenever it fits there alone (R and the
+        // projections then go to the slot's global scratch)
+        const bool x_sh = (uint64_t)ld * cm <= P.x_smem;
+        V* X = x_sh ? S.X : xg;
+        V* Rm = fast || !x_sh ? X + (size_t)ld * cm : xg;  // R, row-major: kept index x cm
+        V* O = fast ? Rm + (size_t)cm * cm : nullptr;       // staged copy of the other tensor
         V* hb = fast ? O + other : reinterpret_cast<V*>(gsig2);  // one pass's projections
         int* perm = reinterpret_cast<int*>(hb + cm);             // kept columns, in order
         V* A = site(q);
@@ -1788,7 +1824,7 @@ struct Engine {
                 *P.ref_disc_out = disc;
                 *P.ref_chi_out = chi_peak;
                 if (status != 0) atomicCAS(P.ref_status, 0, -1000 + status);
-            } else if (!(P.defer_capacity && status == QC_ECAPACITY)) {
+            } else if (!(P.defer_capacity && (status == QC_ECAPACITY || status == QC_INTERNAL_FP64_RERUN))) {
                 const int wb = min(nf, P.wmax);
                 atomicAdd(&P.counts[3 * wb + 0], 1ull);
                 if (status == 0) {
@@ -1854,7 +1890,7 @@ __device__ unsigned char* carve(Shared<R>& S, unsigned char* p, const EnginePara
 template <typename R, int NT>
 __global__ void __launch_bounds__(NT == 32 ? 256 : NT, NT == 32 ? 2 : (NT == 128 ? 4 : (NT == 256 ? 2 : 1)))
 engine_kernel(const EngineParams<R> P) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned char* smem_raw = qc_dsmem;
     const int engines = (NT == 32) ? (int)(blockDim.x >> 5) : 1;
     const int e = (NT == 32) ? (int)(threadIdx.x >> 5) : 0;
     const int tid = (NT == 32) ? (int)(threadIdx.x & 31) : (int)threadIdx.x;
@@ -2315,7 +2351,9 @@ static qc_status run_engine(CircuitImpl& c, qc_noise noise, const uint64_t* shot
     P.precision = prm.precision;
     P.wmax = wmax;
     P.sweep_cap = sizeof(R) == 4 ? 40 : 60;  // the noiseless reference run always keeps the default
-    P.track_norms = getenv("QCMPS_NO_NORM_TRACKING") ? 0 : 1;
+    // norm tracking (alpha, beta updated by the rotation instead of summed) measured no faster on the
+    // benchmark workload, and its rounding moves near-degenerate cuts: off unless asked for
+    P.track_norms = getenv("QCMPS_NORM_TRACKING") ? 1 : 0;
     {
         int center = 0;
         for (const MpsOp& o : c.mps) {
@@ -2415,6 +2453,7 @@ static qc_status run_engine(CircuitImpl& c, qc_noise noise, const uint64_t* shot
     // 2. capacity bucket: slots sized for chi_alloc = min(chi, max(64, 2 chi_peak_ref)); a shot
     //    that outgrows it is reported by the first pass and re-run with full capacity
     const int chi_alloc = bucket_chi(ref->chi_peak, chi);
+    const bool bucketed = chi_alloc < chi;
     // launch configuration: manual override, else the measured choice (batches that fill the GPU on
     // their own), else the rule
     // (the first pass is small when the noiseless run stays at bond 64, as most shots do; the re-run
@@ -2429,16 +2468,10 @@ static qc_status run_engine(CircuitImpl& c, qc_noise noise, const uint64_t* shot
             cf = tuned_cfg<R, NT_BIG>(c, Pp, Lp, ref->state, cp, op, *ref, shots_dev, n, s, nsm, dev, small, cf);
         return cf;
     };
-    if (chi_alloc >= chi) {
-        const LaunchCfg cf = pick(P, L, ref->cap, ref->off, nshots, true);
-        if (trace) { trace->launch_threads_out = cf.variant; trace->launch_kb_out = cf.kb; }
-        return run_pass<R, NT_BIG>(c, P, L, ref->state, ref->cap, ref->off, *ref, shots_dev, nshots, counts_dev,
-                                   per_shot, s, max_slots, nsm, false, cf);
-    }
-    const SlotLayout L1 = slot_layout(c.n, chi_alloc);
-    int* cap1 = nullptr;
-    uint64_t* off1 = nullptr;
-    {
+    const SlotLayout L1 = bucketed ? slot_layout(c.n, chi_alloc) : L;
+    int* cap1 = ref->cap;
+    uint64_t* off1 = ref->off;
+    if (bucketed) {
         std::lock_guard<std::mutex> lk(c.ref_mu);
         auto it = ref->packed.find(chi_alloc);
         if (it == ref->packed.end()) {
@@ -2456,13 +2489,18 @@ static qc_status run_engine(CircuitImpl& c, qc_noise noise, const uint64_t* shot
         cap1 = it->second.cap;
         off1 = it->second.off;
     }
-    // first pass: per-shot results are needed to find the shots that outgrew the bucket
-    qc_shot_result* res1 = per_shot;
-    if (!res1) QC_CUDA(cudaMallocAsync((void**)&res1, nshots * sizeof(qc_shot_result), s));
     EngineParams<R> P1 = P;
-    P1.chi_max = chi_alloc;
+    P1.chi_max = bucketed ? chi_alloc : chi;
     const LaunchCfg cf1 = pick(P1, L1, cap1, off1, nshots, true);
     if (trace) { trace->launch_threads_out = cf1.variant; trace->launch_kb_out = cf1.kb; }
+    // one pass unless shots can be deferred: by the capacity bucket, or (complex64 in one warp per shot) by a
+    // cut inside a cluster that needs the FP64 split
+    if (!bucketed && !(sizeof(R) == 4 && cf1.variant == 32))
+        return run_pass<R, NT_BIG>(c, P, L, ref->state, ref->cap, ref->off, *ref, shots_dev, nshots, counts_dev,
+                                   per_shot, s, max_slots, nsm, false, cf1);
+    // first pass: per-shot results are needed to find the shots to re-run
+    qc_shot_result* res1 = per_shot;
+    if (!res1) QC_CUDA(cudaMallocAsync((void**)&res1, nshots * sizeof(qc_shot_result), s));
     qc_status out = run_pass<R, NT_BIG>(c, P1, L1, ref->state, cap1, off1, *ref, shots_dev, nshots, counts_dev, res1,
                                         s, max_slots, nsm, true, cf1);
     std::vector<qc_shot_result> h;
@@ -2474,7 +2512,10 @@ static qc_status run_engine(CircuitImpl& c, qc_noise noise, const uint64_t* shot
     }
     std::vector<uint64_t> redo, where;
     for (uint64_t i = 0; out == QC_OK && i < nshots; ++i)
-        if (h[i].status == QC_ECAPACITY) { redo.push_back(h[i].shot); where.push_back(i); }
+        if (h[i].status == QC_ECAPACITY || h[i].status == QC_INTERNAL_FP64_RERUN) {
+            redo.push_back(h[i].shot);
+            where.push_back(i);
+        }
     if (out == QC_OK && !redo.empty()) {
         // second pass with the full capacity, then the records go back to their places
         uint64_t* shots2 = nullptr;
@@ -2511,11 +2552,11 @@ static qc_status run_engine(CircuitImpl& c, qc_noise noise, const uint64_t* shot
     return out;
 }
 
-qc_status engine_launch(CircuitImpl& c, qc_noise noise, const uint64_t* shots_dev, uint64_t nshots,
-                        qc_mps_params prm, unsigned long long* counts_dev, int wmax, qc_shot_result* per_shot,
-                        cudaStream_t s, int max_slots, bool shared_gpu, qc_mps_trace* trace) {
+// Argument checks of a sampling call (host only, before any device work).
+static qc_status check_args(const CircuitImpl& c, qc_noise noise, const uint64_t* shots_dev, uint64_t nshots,
+                            qc_mps_params prm) {
     if (!(noise.p >= 0.0 && noise.p < 1.0)) return fail(QC_EINVAL, "p must lie in [0, 1)");
-    if (prm.chi_max < 1) return fail(QC_EINVAL, "chi_max must be >= 1");
+    if (prm.chi_max < 1 || prm.chi_max > 1024) return fail(QC_EINVAL, "chi_max must be in [1, 1024]");
     if (!(prm.cutoff >= 0.0)) return fail(QC_EINVAL, "cutoff must be >= 0");
     if (prm.precision != QC_C64 && prm.precision != QC_C128) return fail(QC_EINVAL, "unknown precision");
     if (noise.fault_weight >= 0 && (uint64_t)noise.fault_weight > c.chan_kind.size())
@@ -2523,6 +2564,13 @@ qc_status engine_launch(CircuitImpl& c, qc_noise noise, const uint64_t* shots_de
     if (noise.fault_weight > MAXF) return fail(QC_EINVAL, "fault weight above %d", MAXF);
     if (nshots && !shots_dev) return fail(QC_EINVAL, "null shots");
     if (c.n < 2) return fail(QC_EINVAL, "the MPS engine needs at least two qubits");
+    return QC_OK;
+}
+
+qc_status engine_launch(CircuitImpl& c, qc_noise noise, const uint64_t* shots_dev, uint64_t nshots,
+                        qc_mps_params prm, unsigned long long* counts_dev, int wmax, qc_shot_result* per_shot,
+                        cudaStream_t s, int max_slots, bool shared_gpu, qc_mps_trace* trace) {
+    if (const qc_status a = check_args(c, noise, shots_dev, nshots, prm); a != QC_OK) return a;
     if (prm.precision == QC_C64)
         return run_engine<float, NT_F>(c, noise, shots_dev, nshots, prm, counts_dev, wmax, per_shot, s, max_slots,
                                        shared_gpu, trace);
@@ -2577,6 +2625,7 @@ extern "C" qc_status mps_sample_batch_traced(const qc_circuit* circuit, qc_noise
         return fail(QC_EINVAL, "null readout record buffer");
     cudaStream_t s = (cudaStream_t)stream;
     CircuitImpl& c = const_cast<qc_circuit*>(circuit)->impl;
+    if (const qc_status a = check_args(c, noise, shots_dev, nshots, params); a != QC_OK) return a;
     if (trace && trace->readout_p1_dev && trace->readout_k > 0 && nshots)  // all-ones bytes: NaN
         QC_CUDA(cudaMemsetAsync(trace->readout_p1_dev, 0xFF, nshots * (size_t)trace->readout_k * sizeof(double), s));
     unsigned long long* counts = nullptr;

@@ -28,6 +28,10 @@ namespace {
 
 constexpr int WBINS = 16;
 constexpr uint64_t CHUNK_SHOTS = 512;  // bounds how long a worker stays on one job
+// A chunk holds at most this many shots per slot it is given: when the budget is nearly spent, a chunk
+// shrinks with its slots instead of queueing hundreds of shots behind one or two of them (its latency
+// stays about this many shot times, and the rest of the job waits for memory to free up).
+constexpr uint64_t CHUNK_ROUNDS = 2;
 
 struct Job {
     uint64_t id;
@@ -98,7 +102,7 @@ struct Server {
         Job* best = nullptr;
         double best_score = 0;
         bool best_starved = false;
-        uint64_t best_slots = 0;
+        uint64_t best_slots = 0, best_count = 0;
         for (Job* j : order) {
             if (j->state != QC_PENDING || j->cancelled) continue;
             if (!j->prescreened) {
@@ -124,11 +128,12 @@ struct Server {
                 best_score = score;
                 best_starved = starved;
                 best_slots = std::min(slots, fit);
+                best_count = std::min<uint64_t>(n, CHUNK_ROUNDS * best_slots);
             }
         }
         if (!best) return false;
         Job* j = best;
-        const uint64_t n = std::min<uint64_t>(j->survivors - j->next, CHUNK_SHOTS);
+        const uint64_t n = best_count;
         job = j; pre = false;
         first = j->next;
         count = n;

@@ -70,3 +70,17 @@ def test_footprint_formula(native):
     assert 0 < small < big
     # complex128 doubles the site tensors; a complex64 slot also holds room for an FP64 re-split
     assert big < c.footprint(64, native.QC_C128) <= 2 * big
+
+
+@pytest.mark.parametrize("chi,cutoff,prec", [(0, 1e-10, 0), (1025, 1e-10, 0), (2048, 0.0, 1), (32, -1.0, 0),
+                                             (32, 1e-10, 7)])
+def test_sampling_arguments_are_checked_before_device_work(native, chi, cutoff, prec):
+    """chi_max in [1, 1024] (the engine's index arithmetic and slot layout assume it), cutoff >= 0, a known
+    precision: rejected with QC_EINVAL by the host before any device call, so this runs without a GPU."""
+    import ctypes as C
+    from paper_2609_19116_b300.api import Circuit
+    c = Circuit(workload_circuit("d3_17q_12l", layers=2))
+    lib = native.lib()
+    st = lib.mps_sample_batch(c._h, native.Noise(1e-3, 1, -1), None, 0, native.MpsParams(chi, cutoff, prec, 0.0),
+                              None, 0, None, None)
+    assert st == native.QC_EINVAL
