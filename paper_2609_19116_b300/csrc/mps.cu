@@ -49,6 +49,7 @@ __device__ __forceinline__ V dot_conj(const V* u, const V* t, size_t ts, int n) 
     if constexpr (sizeof(V) == 8) {
         float2 a0 = make_float2(0.f, 0.f), a1 = a0, b0 = a0, b1 = a0;
         int i = 0;
+#pragma unroll 1
         for (; i + 1 < n; i += 2) {
             const float2 x0 = u[i], y0 = t[(size_t)i * ts], x1 = u[i + 1], y1 = t[(size_t)(i + 1) * ts];
             a0 = __ffma2_rn(make_float2(x0.x, x0.x), y0, a0);                      // (ux tx, ux ty)
@@ -66,6 +67,7 @@ __device__ __forceinline__ V dot_conj(const V* u, const V* t, size_t ts, int n) 
     } else {
         V a0 = cmk<V>(0, 0), a1 = a0;
         int i = 0;
+#pragma unroll 1
         for (; i + 1 < n; i += 2) {
             a0 = cfmac(u[i], t[(size_t)i * ts], a0);
             a1 = cfmac(u[i + 1], t[(size_t)(i + 1) * ts], a1);
@@ -79,6 +81,7 @@ __device__ __forceinline__ V dot_plain(const V* t, const V* u, int n) {  // sum_
     if constexpr (sizeof(V) == 8) {
         float2 a0 = make_float2(0.f, 0.f), a1 = a0, b0 = a0, b1 = a0;
         int i = 0;
+#pragma unroll 1
         for (; i + 1 < n; i += 2) {
             const float2 x0 = t[i], y0 = u[i], x1 = t[i + 1], y1 = u[i + 1];
             a0 = __ffma2_rn(make_float2(x0.x, x0.x), y0, a0);                       // (tx ux, tx uy)
@@ -96,6 +99,7 @@ __device__ __forceinline__ V dot_plain(const V* t, const V* u, int n) {  // sum_
     } else {
         V a0 = cmk<V>(0, 0), a1 = a0;
         int i = 0;
+#pragma unroll 1
         for (; i + 1 < n; i += 2) {
             a0 = cfma(t[i], u[i], a0);
             a1 = cfma(t[i + 1], u[i + 1], a1);
@@ -162,7 +166,6 @@ struct EngineParams {
     int sweep_cap;
     unsigned long long* phase_cycles;  // optional [8]: SM cycles per phase of the shots, summed
     int use_tc;                // CTA variants: two-site contractions of large theta on the tensor cores
-    int track_norms;           // Jacobi tracks the column norms instead of summing them every pair
     double* trace_p1;          // optional [ntasks x trace_k]: readout probabilities of each shot
     const uint64_t* trace_pos; // optional: record row of each task (the capacity re-run pass)
     int trace_k;
@@ -324,6 +327,7 @@ struct Engine {
         const V g00 = u[0], g01 = u[1], g10 = u[2], g11 = u[3];
         const int cl = S.dims[q], cr = S.dims[q + 1];
         V* a = site(q);
+#pragma unroll 1
         for (int e = tid_; e < cl * cr; e += NT) {
             const int l = e / cr, r = e - l * cr;
             V* p0 = a + (l * 2) * cr + r;
@@ -356,6 +360,7 @@ struct Engine {
         using VS = typename VecOf<RS>::T;
         if constexpr (sizeof(RS) == 4) {
             float2 sa = make_float2(0.f, 0.f), sb = sa, sg = sa, sh = sa;
+#pragma unroll 1
             for (int i = gl; i < rows; i += g) {
                 const float2 x = a[i], y = b[i];
                 sa = __ffma2_rn(x, x, sa);
@@ -368,6 +373,7 @@ struct Engine {
             gr = sg.x + sg.y;
             gi = sh.x - sh.y;
         } else {
+#pragma unroll 1
             for (int i = gl; i < rows; i += g) {
                 const VS x = a[i], y = b[i];
                 al = fma(x.x, x.x, fma(x.y, x.y, al));
@@ -387,6 +393,7 @@ struct Engine {
         if constexpr (sizeof(RS) == 4) {
             const float2 cc = make_float2(c, c), nw = make_float2(-wr, -wr), ws = make_float2(wi, -wi);
             const float2 wp = make_float2(wr, wr);
+#pragma unroll 1
             for (int i = gl; i < rows; i += g) {
                 const float2 x = a[i], y = b[i];
                 float2 t = __fmul2_rn(nw, y);                          // -w y
@@ -398,6 +405,7 @@ struct Engine {
                 b[i] = u;
             }
         } else {
+#pragma unroll 1
             for (int i = gl; i < rows; i += g) {
                 const VS x = a[i], y = b[i];
                 const RS wyx = wr * y.x - wi * y.y, wyy = wr * y.y + wi * y.x;  // w y
@@ -438,83 +446,6 @@ struct Engine {
         return 0;
     }
 
-    // gamma = a^H b only (the column norms are tracked), same lane layout as pair_dots.
-    template <typename RS>
-    __device__ __forceinline__ void pair_gamma(const typename VecOf<RS>::T* a,
-                                               const typename VecOf<RS>::T* b, int rows, int gl, int g,
-                                               RS& gr, RS& gi) {
-        using VS = typename VecOf<RS>::T;
-        if constexpr (sizeof(RS) == 4) {
-            float2 sg = make_float2(0.f, 0.f), sh = sg;
-            for (int i = gl; i < rows; i += g) {
-                const float2 x = a[i], y = b[i];
-                sg = __ffma2_rn(x, y, sg);                            // (x.re y.re, x.im y.im)
-                sh = __ffma2_rn(x, make_float2(y.y, y.x), sh);         // (x.re y.im, x.im y.re)
-            }
-            gr = sg.x + sg.y;
-            gi = sh.x - sh.y;
-        } else {
-            for (int i = gl; i < rows; i += g) {
-                const VS x = a[i], y = b[i];
-                gr = fma(x.x, y.x, fma(x.y, y.y, gr));
-                gi = fma(x.x, y.y, fma(-x.y, y.x, gi));
-            }
-        }
-    }
-
-    // pair_step with the squared column norms tracked in na, nb: a rotation that zeroes gamma changes
-    // them exactly to alpha - t |gamma| and beta + t |gamma| (t the tangent of the angle), so only gamma
-    // is summed over the rows.  The norms are recomputed at the start of every sweep.
-    template <typename RS>
-    __device__ __forceinline__ int pair_step_n(typename VecOf<RS>::T* a, typename VecOf<RS>::T* b, int rows, int gl,
-                                               int g, bool act, RS tol, RS floor2, RS* na, RS* nb) {
-        RS gr = 0, gi = 0;
-        RS al = 0, be = 0;
-        if (act) {
-            al = *na;
-            be = *nb;
-            pair_gamma(a, b, rows, gl, g, gr, gi);
-        }
-        for (int o = g >> 1; o > 0; o >>= 1) {
-            gr += __shfl_xor_sync(0xFFFFFFFFu, gr, o);
-            gi += __shfl_xor_sync(0xFFFFFFFFu, gi, o);
-        }
-        const RS g2 = gr * gr + gi * gi;
-        if (act && g2 > tol * tol * (al * be) && g2 > (RS)0 && fmin(al, be) > floor2) {
-            const RS rg = rs_sqrt(g2);                    // 1 / |gamma|
-            const RS zeta = (be - al) * (RS)0.5 * rg;
-            const RS t = fdiv(zeta >= 0 ? (RS)1 : (RS)-1, fabs(zeta) + sqrt((RS)1 + zeta * zeta));
-            const RS c = rs_sqrt((RS)1 + t * t), sn = c * t;
-            pair_rotate(a, b, rows, gl, g, c, sn * gr * rg, -sn * gi * rg);
-            if (gl == 0) {
-                const RS tg = t * g2 * rg;  // t |gamma|
-                *na = al - tg;
-                *nb = be + tg;
-            }
-            return 1;
-        }
-        return 0;
-    }
-
-    // Squared norms of the columns of X into nrm (lane groups as in the sweeps).
-    template <typename RS>
-    __device__ void column_norms(const typename VecOf<RS>::T* X, int rows, int cols, int ld, RS* nrm) {
-        const int wid = tid_ >> 5;
-        constexpr int NW = NT / 32;
-        int G, g, grp, gl;
-        lane_groups(cols, rows, G, g, grp, gl);
-        for (int base = wid * G; base < cols; base += NW * G) {
-            const int j = base + grp;
-            RS sq = 0;
-            if (j < cols) {
-                const auto* col = X + (size_t)j * ld;
-                for (int i = gl; i < rows; i += g) sq = fma(col[i].x, col[i].x, fma(col[i].y, col[i].y, sq));
-            }
-            for (int o = g >> 1; o > 0; o >>= 1) sq += __shfl_xor_sync(0xFFFFFFFFu, sq, o);
-            if (j < cols && gl == 0) nrm[j] = sq;
-        }
-    }
-
     // Lane groups for `pairs` concurrent pairs: G groups of g = 32 / G lanes per warp (G a power of
     // two, up to one lane per pair), so that small matrices keep every lane busy and reduce over short
     // shuffle trees.
@@ -541,7 +472,7 @@ struct Engine {
     // matrix that lives in global memory block by block), so the loops take shared-memory addressing.
     template <typename RS>
     __device__ bool jacobi(typename VecOf<RS>::T* X, int rows, int cols, int ld, RS floor2, int max_sweeps = 0,
-                           int* any_rotation = nullptr, RS* nrm = nullptr) {
+                           int* any_rotation = nullptr) {
         if constexpr (sizeof(RS) == sizeof(R)) X = as_smem(X);
         const int wid = tid_ >> 5;
         constexpr int NW = NT / 32;
@@ -550,13 +481,12 @@ struct Engine {
         int G, g, grp, gl;
         lane_groups(half, rows, G, g, grp, gl);
         const int cap = max_sweeps > 0 ? max_sweeps : P.sweep_cap;
+#pragma unroll 1
         for (int sweep = 0; sweep < cap; ++sweep) {
             int rotated = 0;
-            if (nrm) {
-                column_norms<RS>(X, rows, cols, ld, nrm);
-                bsync<NT>();
-            }
+#pragma unroll 1
             for (int k = 0; k < cm1; ++k) {
+#pragma unroll 1
                 for (int base = wid * G; base < half; base += NW * G) {
                     const int pr = base + grp;
                     const bool act = pr < half;
@@ -567,11 +497,7 @@ struct Engine {
                     ib -= ib >= cm1 ? cm1 : 0;
                     const int ca = sa == 0 ? 0 : 1 + ia;
                     const int cb = 1 + ib;
-                    if (nrm)
-                        rotated |= pair_step_n(X + (size_t)ca * ld, X + (size_t)cb * ld, rows, gl, g, act, tol, floor2,
-                                               nrm + ca, nrm + cb);
-                    else
-                        rotated |= pair_step(X + (size_t)ca * ld, X + (size_t)cb * ld, rows, gl, g, act, tol, floor2);
+                    rotated |= pair_step(X + (size_t)ca * ld, X + (size_t)cb * ld, rows, gl, g, act, tol, floor2);
                 }
                 bsync<NT>();
             }
@@ -598,7 +524,9 @@ struct Engine {
         int G, g, grp, gl;
         lane_groups(ns, rows, G, g, grp, gl);
         int rotated = 0;
+#pragma unroll 1
         for (int k = 0; k < nl; ++k) {
+#pragma unroll 1
             for (int base = wid * G; base < ns; base += NW * G) {
                 const int i = base + grp;
                 const bool act = i < ns;
@@ -627,9 +555,12 @@ struct Engine {
         const int lw = rows + 1;
         const int nb = (cols + bw - 1) / bw;
         const int nbp = nb + (nb & 1);  // an even number of blocks (the last may be a dummy)
+#pragma unroll 1
         for (int sweep = 0; sweep < P.sweep_cap; ++sweep) {
             int rot = 0;
+#pragma unroll 1
             for (int k = 0; k < nbp - 1; ++k) {
+#pragma unroll 1
                 for (int pr = 0; pr < nbp / 2; ++pr) {
                     const int sa = pr, sb = nbp - 1 - pr;
                     int ia = sa - 1 + k, ib = sb - 1 + k;
@@ -642,6 +573,7 @@ struct Engine {
                     const int nj = bj < nb ? min(cols, j0 + bw) - j0 : 0;
                     const int nc = ni + nj;
                     if (nc == 0) continue;
+#pragma unroll 1
                     for (int e = tid_; e < nc * rows; e += NT) {
                         const int c = e / rows, i = e - c * rows;
                         W[(size_t)c * lw + i] = c < ni ? X[(size_t)(i0 + c) * ld + i] : X[(size_t)(j0 + c - ni) * ld + i];
@@ -652,6 +584,7 @@ struct Engine {
                         if (nj >= 2) jacobi(W + (size_t)ni * lw, rows, nj, lw, floor2, 1, &rot);
                     }
                     if (ni && nj) rot |= cross_pass(W, rows, ni, nj, lw, floor2);
+#pragma unroll 1
                     for (int e = tid_; e < nc * rows; e += NT) {
                         const int c = e / rows, i = e - c * rows;
                         const auto v = W[(size_t)c * lw + i];
@@ -680,11 +613,13 @@ struct Engine {
             int G = 1;
             while (G < cpw && G < 32) G <<= 1;
             const int g = 32 / G, grp = lane / g, gl = lane - grp * g;
+#pragma unroll 1
             for (int base = wid * G; base < cols; base += NW * G) {
                 const int j = base + grp;
                 RS sq = 0;
                 if (j < cols) {
                     const auto* col = X + (size_t)j * ld;
+#pragma unroll 1
                     for (int i = gl; i < rows; i += g) sq = fma(col[i].x, col[i].x, fma(col[i].y, col[i].y, sq));
                 }
                 for (int o = g >> 1; o > 0; o >>= 1) sq += __shfl_xor_sync(0xFFFFFFFFu, sq, o);
@@ -692,9 +627,11 @@ struct Engine {
             }
         }
         bsync<NT>();
+#pragma unroll 1
         for (int j = tid_; j < cols; j += NT) {
             const RS sj = sig2[j];
             int rk = 0;
+#pragma unroll 1
             for (int k = 0; k < cols; ++k) {
                 const RS sk = sig2[k];
                 rk += (sk > sj) || (sk == sj && k < j);
@@ -714,6 +651,7 @@ struct Engine {
             const int k0 = min(cols, lane * c), k1 = min(cols, k0 + c);
             double loc = 0;
             int nzl = 0;
+#pragma unroll 1
             for (int k = k0; k < k1; ++k) {
                 const RS v = sig2[perm[k]];
                 loc += (double)v;
@@ -731,6 +669,7 @@ struct Engine {
             const double thr = P.cutoff * tot;
             int cnt = 0;
             double tail = after;
+#pragma unroll 1
             for (int k = k1 - 1; k >= k0; --k) {
                 tail += (double)sig2[perm[k]];
                 cnt += (k >= 1 && tail > thr);
@@ -739,6 +678,7 @@ struct Engine {
             r = min(r, P.chi_trunc);
             r = min(r, max(nz, 1));
             double kl = 0, tl = 0;
+#pragma unroll 1
             for (int k = k0; k < k1; ++k) {
                 const double v = (double)sig2[perm[k]];
                 if (k < r) kl += v; else tl += v;
@@ -840,9 +780,13 @@ struct Engine {
         const uint32_t idesc = tc::idesc_tf32(128, 32);
         const int warp = tid_ >> 5, lane = tid_ & 31, quarter = warp & 3, wgrp = warp >> 2;
         const V* gt = S.gate;
+#pragma unroll 1
         for (int mt = 0; mt < m; mt += 128) {
+#pragma unroll 1
             for (int r0 = 0; r0 < cr; r0 += 16) {
+#pragma unroll 1
                 for (int kc = 0; kc < cm; kc += KC) {
+#pragma unroll 1
                     for (int e = tid_; e < TA; e += NT) {  // A rows mt.., K kc..
                         const int rr = e / KC, kk = e - rr * KC;
                         const int i = mt + rr, k = kc + kk;
@@ -853,6 +797,7 @@ struct Engine {
                         tc::split_tf32(a.y, h, l); sa[2 * TA + o] = h; sa[3 * TA + o] = l;
                         tc::split_tf32(a.x + a.y, h, l); sa[4 * TA + o] = h; sa[5 * TA + o] = l;
                     }
+#pragma unroll 1
                     for (int e = tid_; e < TB; e += NT) {  // B columns (t', r0 + jj), K kc..
                         const int jj = e / KC, kk = e - jj * KC;
                         const int r = r0 + (jj & 15), tp = jj >> 4, k = kc + kk;
@@ -896,6 +841,7 @@ struct Engine {
                 // epilogue: this thread's row i = (l, s'); column pieces p of 8 values of r
                 const int i = mt + quarter * 32 + lane;
                 const uint32_t ta = tmem_ + ((uint32_t)(quarter * 32) << 16);
+#pragma unroll 1
                 for (int pc = wgrp; pc < 2; pc += NT / 128) {
                     float p1a[8], p2a[8], p3a[8], p1b[8], p2b[8], p3b[8];
                     tc::tmem_ld8(ta + 0 + pc * 8, p1a);
@@ -971,6 +917,7 @@ struct Engine {
             // warp mode: borrow the CTA's large work area (bounded wait; the global path otherwise)
             int got = 0;
             if (tid_ == 0) {
+#pragma unroll 1
                 for (int it = 0; it < (1 << 22); ++it) {
                     if (atomicCAS(S.big_lock, 0, 1) == 0) { got = 1; break; }
                     __nanosleep(256);
@@ -999,7 +946,9 @@ struct Engine {
         if (fast) {
             V* As = W + (size_t)ld * cols;
             V* Bs = As + (size_t)m * cm;
+#pragma unroll 1
             for (int e = tid_; e < m * cm; e += NT) As[e] = A[e];
+#pragma unroll 1
             for (int e = tid_; e < cm * n; e += NT) Bs[e] = B[e];
             A = As;
             B = Bs;
@@ -1021,6 +970,7 @@ struct Engine {
                 return SPLIT_FAIL;
             }
         }
+#pragma unroll 1
         for (int e = on_tc ? cl * cr : tid_; e < cl * cr; e += NT) {
             const int l = e / cr, r = e - l * cr;
             VS th[4];
@@ -1030,6 +980,7 @@ struct Engine {
             const V* a1 = a0 + cm;
             if constexpr (sizeof(RS) == 4) {  // complex MACs as two paired FP32 FMAs each
                 float2 t0 = make_float2(0.f, 0.f), t1 = t0, t2 = t0, t3 = t0;
+#pragma unroll 1
                 for (int k = 0; k < cm; ++k) {
                     const float2 x0 = a0[k], x1 = a1[k];
                     const float2 y0 = B[(size_t)k * n + r], y1 = B[(size_t)k * n + cr + r];
@@ -1043,6 +994,7 @@ struct Engine {
                 }
                 th[0] = t0; th[1] = t1; th[2] = t2; th[3] = t3;
             } else {
+#pragma unroll 1
                 for (int k = 0; k < cm; ++k) {
                     const VS x0 = widen<VS>(a0[k]), x1 = widen<VS>(a1[k]);
                     const VS y0 = widen<VS>(B[(size_t)k * n + r]), y1 = widen<VS>(B[(size_t)k * n + cr + r]);
@@ -1066,6 +1018,7 @@ struct Engine {
         }
         if (fast) {  // A and B are consumed: keep theta' in T for the projection after the split
             bsync<NT>();
+#pragma unroll 1
             for (int e = tid_; e < m * n; e += NT) {
                 const int i = e / n, j = e - i * n;
                 const VS v = xt ? X[(size_t)j * ld + i] : X[(size_t)i * ld + j];
@@ -1094,7 +1047,7 @@ struct Engine {
         gmem_updates += in_global ? 1 : 0;
         tock(PH_CONTRACT);
         if (!(blocked ? jacobi_blocked<RS>(X, rows, cols, ld, floor2, reinterpret_cast<VS*>(S.X), bw)
-                      : jacobi<RS>(X, rows, cols, ld, floor2, 0, nullptr, P.track_norms ? sig2 : nullptr))) {
+                      : jacobi<RS>(X, rows, cols, ld, floor2))) {
             status = QC_ENOCONV;
             release_big(locked);
             return SPLIT_FAIL;
@@ -1116,6 +1069,7 @@ struct Engine {
             return SPLIT_FAIL;
         }
         // the kept singular values, once per column: sig2[j] <- sqrt(sig2[j])
+#pragma unroll 1
         for (int k = tid_; k < r; k += NT) {
             const int j = perm[k];
             const RS sg = sig2[j];
@@ -1123,6 +1077,7 @@ struct Engine {
         }
         bsync<NT>();
         // normalise the kept columns to unit length (the orthonormal factor)
+#pragma unroll 1
         for (int e = tid_; e < r * rows; e += NT) {
             const int k = e / rows, i = e - k * rows;
             const int j = perm[k];
@@ -1136,11 +1091,13 @@ struct Engine {
         V* Bs = site(q + 1);
         if (xt && right) {
             // X = theta' = U S V^H:  A[q] = U (cl, 2, r);  A[q+1] = scale * U^H theta' (r, 2, cr)
+#pragma unroll 1
             for (int e = tid_; e < m * r; e += NT) {
                 const int i = e / r, k = e - i * r;
                 const VS u = X[(size_t)perm[k] * ld + i];
                 As[e] = cmk<V>(u.x, u.y);
             }
+#pragma unroll 1
             for (int e = tid_; e < r * n; e += NT) {
                 const int k = e / n, j = e - k * n;
                 const VS acc = dot_conj(X + (size_t)perm[k] * ld, T + j, (size_t)n, m);
@@ -1148,11 +1105,13 @@ struct Engine {
             }
         } else if (!xt && !right) {
             // X = theta'^H = U' S V'^H:  A[q+1] = U'^H (r, 2, cr);  A[q] = scale * theta' U' (cl, 2, r)
+#pragma unroll 1
             for (int e = tid_; e < r * n; e += NT) {
                 const int k = e / n, j = e - k * n;
                 const VS u = X[(size_t)perm[k] * ld + j];
                 Bs[e] = cmk<V>(u.x, -u.y);
             }
+#pragma unroll 1
             for (int e = tid_; e < m * r; e += NT) {
                 const int i = e / r, k = e - i * r;
                 const VS acc = dot_plain(T + (size_t)i * n, X + (size_t)perm[k] * ld, n);
@@ -1161,12 +1120,14 @@ struct Engine {
         } else if (xt) {
             // X = theta' = U S V^H, centre to the left:  A[q] = scale * U S (cl, 2, r);
             // A[q+1] = V^H = S^-1 U^H theta' (r, 2, cr)
+#pragma unroll 1
             for (int e = tid_; e < m * r; e += NT) {
                 const int i = e / r, k = e - i * r;
                 const RS f = scale * sig2[perm[k]];
                 const VS u = X[(size_t)perm[k] * ld + i];
                 As[e] = cmk<V>(u.x * f, u.y * f);
             }
+#pragma unroll 1
             for (int e = tid_; e < r * n; e += NT) {
                 const int k = e / n, j = e - k * n;
                 const VS acc = dot_conj(X + (size_t)perm[k] * ld, T + j, (size_t)n, m);
@@ -1177,12 +1138,14 @@ struct Engine {
         } else {
             // X = theta'^H = U' S V'^H (theta' = V' S U'^H), centre to the right:
             // A[q] = V' = theta' U' S^-1 (cl, 2, r);  A[q+1] = scale * S U'^H (r, 2, cr)
+#pragma unroll 1
             for (int e = tid_; e < r * n; e += NT) {
                 const int k = e / n, j = e - k * n;
                 const RS f = scale * sig2[perm[k]];
                 const VS u = X[(size_t)perm[k] * ld + j];
                 Bs[e] = cmk<V>(u.x * f, -u.y * f);
             }
+#pragma unroll 1
             for (int e = tid_; e < m * r; e += NT) {
                 const int i = e / r, k = e - i * r;
                 const VS acc = dot_plain(T + (size_t)i * n, X + (size_t)perm[k] * ld, n);
@@ -1216,17 +1179,21 @@ struct Engine {
     __device__ int gram_schmidt(V* X, int rows, int cols, int ld, V* Rm, V* hb, int* perm, R floor2,
                                 double& dropped) {
         int k = 0;
+#pragma unroll 1
         for (int j = 0; j < cols; ++j) {
             V* x = X + (size_t)j * ld;
             R part = 0;
+#pragma unroll 1
             for (int i = tid_; i < rows; i += NT) part = fma(x[i].x, x[i].x, fma(x[i].y, x[i].y, part));
             R nold = sum_r(part), nnow = nold;
+#pragma unroll 1
             for (int pass = 0; pass < 4 && k > 0; ++pass) {
                 {  // h_i = <q_i, x>: the k dot products spread over lane groups (short chains)
                     const int wid = tid_ >> 5;
                     constexpr int NW = NT / 32;
                     int G, g, grp, gl;
                     lane_groups(k, rows, G, g, grp, gl);
+#pragma unroll 1
                     for (int base = wid * G; base < k; base += NW * G) {
                         const int i = base + grp;
                         const bool act = i < k;
@@ -1235,6 +1202,7 @@ struct Engine {
                         if (act) {
                             if constexpr (sizeof(R) == 4) {  // paired FP32 FMAs, as in the Jacobi
                                 float2 s1 = make_float2(0.f, 0.f), s2 = s1;
+#pragma unroll 1
                                 for (int t = gl; t < rows; t += g) {
                                     const float2 u0 = qi[t], x0 = x[t];
                                     s1 = __ffma2_rn(u0, x0, s1);                          // (q.re x.re, q.im x.im)
@@ -1243,6 +1211,7 @@ struct Engine {
                                 hr = s1.x + s1.y;
                                 hi = s2.x - s2.y;
                             } else {
+#pragma unroll 1
                                 for (int t = gl; t < rows; t += g) {
                                     hr = fma(qi[t].x, x[t].x, fma(qi[t].y, x[t].y, hr));
                                     hi = fma(qi[t].x, x[t].y, fma(-qi[t].y, x[t].x, hi));
@@ -1262,6 +1231,7 @@ struct Engine {
                 }
                 bsync<NT>();
                 part = 0;
+#pragma unroll 1
                 for (int t = tid_; t < rows; t += NT) {  // x -= sum_i h_i q_i (two partial sums)
                     V acc = x[t], acc1 = cmk<V>(0, 0);
                     int i = 0;
@@ -1287,6 +1257,7 @@ struct Engine {
             }
             if (nnow > floor2) {
                 const R nr = sqrt(nnow), inv = (R)1 / nr;
+#pragma unroll 1
                 for (int t = tid_; t < rows; t += NT) x[t] = cmk<V>(x[t].x * inv, x[t].y * inv);
                 if (tid_ == 0) {
                     Rm[(size_t)k * cols + j] = cmk<V>(nr, (R)0);
@@ -1329,6 +1300,7 @@ struct Engine {
         V* B = site(q + 1);
         R fro = 0;
         if (right) {
+#pragma unroll 1
             for (int e = tid_; e < m * cm; e += NT) {
                 const int i = e / cm, j = e - i * cm;
                 const V v = A[e];
@@ -1337,6 +1309,7 @@ struct Engine {
             }
             if (fast) for (int e = tid_; e < cm * n; e += NT) O[e] = B[e];
         } else {
+#pragma unroll 1
             for (int e = tid_; e < cm * n; e += NT) {
                 const int k = e / n, j = e - k * n;
                 const V v = B[e];
@@ -1345,6 +1318,7 @@ struct Engine {
             }
             if (fast) for (int e = tid_; e < m * cm; e += NT) O[e] = A[e];
         }
+#pragma unroll 1
         for (int e = tid_; e < cm * cm; e += NT) Rm[e] = cmk<V>(0, 0);
         const V* Bo = right ? (fast ? O : B) : B;
         const V* Ao = right ? A : (fast ? O : A);
@@ -1363,34 +1337,42 @@ struct Engine {
         if (dropped > 0 && frod > 0) disc += dropped / frod;
         if (right) {
             // A[q] = Q (cl, 2, r);  A[q+1] = R B (r, 2, cr), R upper triangular in column order
+#pragma unroll 1
             for (int e = tid_; e < r * n; e += NT) {
                 const int kk = e / n, jn = e - kk * n;
                 const V* rrow = Rm + (size_t)kk * cm;
                 V acc = cmk<V>(0, 0);
+#pragma unroll 1
                 for (int j = perm[kk]; j < cm; ++j) acc = cfma(rrow[j], Bo[(size_t)j * n + jn], acc);
                 tcopy[e] = acc;
             }
             bsync<NT>();
+#pragma unroll 1
             for (int e = tid_; e < m * r; e += NT) {
                 const int i = e / r, kk = e - i * r;
                 A[e] = X[(size_t)perm[kk] * ld + i];
             }
+#pragma unroll 1
             for (int e = tid_; e < r * n; e += NT) B[e] = tcopy[e];
         } else {
             // A[q+1] = Q^H (r, 2, cr);  A[q] = A[q] R^H (cl, 2, r)
+#pragma unroll 1
             for (int e = tid_; e < m * r; e += NT) {
                 const int i = e / r, kk = e - i * r;
                 const V* rrow = Rm + (size_t)kk * cm;
                 V acc = cmk<V>(0, 0);
+#pragma unroll 1
                 for (int j = perm[kk]; j < cm; ++j) acc = cfmac(rrow[j], Ao[(size_t)i * cm + j], acc);
                 tcopy[e] = acc;
             }
             bsync<NT>();
+#pragma unroll 1
             for (int e = tid_; e < r * n; e += NT) {
                 const int kk = e / n, jn = e - kk * n;
                 const V u = X[(size_t)perm[kk] * ld + jn];
                 B[e] = cmk<V>(u.x, -u.y);
             }
+#pragma unroll 1
             for (int e = tid_; e < m * r; e += NT) A[e] = tcopy[e];
         }
         bsync<NT>();
@@ -1424,19 +1406,23 @@ struct Engine {
         const int n = 2 * cr;
         R fro = 0;
         if (prod_left) {
+#pragma unroll 1
             for (int e = tid_; e < cl * n; e += NT) {  // C(l, t, r) = sum_m A(l, 0, m) B(m, t, r)
                 const int l = e / n, j = e - l * n;
                 const V* arow = A + (size_t)(2 * l) * cm;
                 V acc = cmk<V>(0, 0);
+#pragma unroll 1
                 for (int k = 0; k < cm; ++k) acc = cfma(arow[k], B[(size_t)k * n + j], acc);
                 tcopy[e] = acc;
                 fro = fma(acc.x, acc.x, fma(acc.y, acc.y, fro));
             }
         } else {
+#pragma unroll 1
             for (int e = tid_; e < 2 * cl * cr; e += NT) {  // C(l, s, r) = sum_m A(l, s, m) B(m, 0, r)
                 const int i = e / cr, r = e - i * cr;
                 const V* arow = A + (size_t)i * cm;
                 V acc = cmk<V>(0, 0);
+#pragma unroll 1
                 for (int k = 0; k < cm; ++k) acc = cfma(arow[k], B[(size_t)(2 * k) * cr + r], acc);
                 tcopy[e] = acc;
                 fro = fma(acc.x, acc.x, fma(acc.y, acc.y, fro));
@@ -1446,13 +1432,17 @@ struct Engine {
         int nb = prod_left ? cr : cl;  // the new bond between q and q+1
         if (nb <= (prod_left ? 2 * cl : 2 * cr) && nb <= P.cap[q + 1]) {
             if (prod_left) {
+#pragma unroll 1
                 for (int e = tid_; e < cl * n; e += NT) A[e] = tcopy[e];
+#pragma unroll 1
                 for (int e = tid_; e < cr * n; e += NT) {
                     const int r1 = e / n, rem = e - r1 * n;
                     B[e] = cmk<V>(rem == r1 ? (R)1 : (R)0, (R)0);  // (r1, s = 0, r2 = r1)
                 }
             } else {
+#pragma unroll 1
                 for (int e = tid_; e < 2 * cl * cr; e += NT) B[e] = tcopy[e];
+#pragma unroll 1
                 for (int e = tid_; e < cl * 2 * cl; e += NT) {
                     const int l1 = e / (2 * cl), rem = e - l1 * 2 * cl;
                     A[e] = cmk<V>(rem == l1 ? (R)1 : (R)0, (R)0);  // (l1, s = 0, l2 = l1)
@@ -1474,6 +1464,7 @@ struct Engine {
             V* Rm = X + (size_t)ld * cols;
             V* hb = fast ? Rm + (size_t)cols * cols : reinterpret_cast<V*>(gsig2);
             int* perm = reinterpret_cast<int*>(hb + cols);
+#pragma unroll 1
             for (int e = tid_; e < rows * cols; e += NT) {
                 if (prod_left) {  // X[r, j] = conj C[j, r]
                     const int j = e / cr, r = e - j * cr;
@@ -1484,6 +1475,7 @@ struct Engine {
                     X[(size_t)j * ld + l] = tcopy[e];
                 }
             }
+#pragma unroll 1
             for (int e = tid_; e < cols * cols; e += NT) Rm[e] = cmk<V>(0, 0);
             const double frod = (double)sum_r(fro);  // sets the numerical floor only: working precision
             const R eps = sizeof(R) == 4 ? (R)FLT_EPSILON : (R)DBL_EPSILON;
@@ -1504,11 +1496,13 @@ struct Engine {
             nb = k;
             if (prod_left) {
                 // A[q](l, t, kk) = conj R[kk, (l, t)];  A[q+1](kk, s, r) = [s = 0] conj Q[r, kk]
+#pragma unroll 1
                 for (int e = tid_; e < cols * k; e += NT) {
                     const int j = e / k, kk = e - j * k;
                     const V u = Rm[(size_t)kk * cols + j];
                     A[e] = cmk<V>(u.x, -u.y);
                 }
+#pragma unroll 1
                 for (int e = tid_; e < k * n; e += NT) {
                     const int kk = e / n, rem = e - kk * n;
                     V v = cmk<V>(0, 0);
@@ -1520,10 +1514,12 @@ struct Engine {
                 }
             } else {
                 // A[q](l, t, kk) = [t = 0] Q[l, kk];  A[q+1](kk, s, r) = R[kk, (s, r)]
+#pragma unroll 1
                 for (int e = tid_; e < cl * 2 * k; e += NT) {
                     const int l = e / (2 * k), rem = e - l * 2 * k;
                     A[e] = rem < k ? X[(size_t)perm[rem] * ld + l] : cmk<V>(0, 0);
                 }
+#pragma unroll 1
                 for (int e = tid_; e < k * cols; e += NT) B[e] = Rm[e];
             }
             if (tid_ == 0) {
@@ -1534,6 +1530,7 @@ struct Engine {
         bsync<NT>();
         if (tid_ == 0) {
             S.dims[q + 1] = nb;
+#pragma unroll 1
             for (int k = 0; k < 4; ++k) {
                 const V t = S.pend[q * 4 + k];
                 S.pend[q * 4 + k] = S.pend[(q + 1) * 4 + k];
@@ -1556,6 +1553,7 @@ struct Engine {
         const V* u = S.pend + q * 4;
         const V g00 = u[0], g01 = u[1], g10 = u[2], g11 = u[3];
         double p0 = 0, p1 = 0;
+#pragma unroll 1
         for (int e = tid_; e < cl * cr; e += NT) {
             const int l = e / cr, r = e - l * cr;
             V* px = a + (l * 2) * cr + r;
@@ -1604,6 +1602,7 @@ struct Engine {
         }
         const R sc = (R)(1.0 / sqrt(po));
         const bool flip = (!is_meas) && outcome == 1;  // reset to |0>: project on 1 then X
+#pragma unroll 1
         for (int e = tid_; e < cl * cr; e += NT) {
             const int l = e / cr, r = e - l * cr;
             V* x0 = a + (l * 2) * cr + r;
@@ -1629,24 +1628,30 @@ struct Engine {
         if (tid_ == 0) E[0] = cmk<V>(1, 0);
         bsync<NT>();
         const V* refsite = P.ref;
+#pragma unroll 1
         for (int q = 0; q < P.nq; ++q) {
             const int ca = P.ref_dims[q], ca2 = P.ref_dims[q + 1];
             const int cb = S.dims[q], cb2 = S.dims[q + 1];
             const V* Aq = site(q);
             const V* Rq = refsite + P.ref_off[q];
             // T1[a][s][b'] = sum_b E[a][b] A[b][s][b']
+#pragma unroll 1
             for (int e = tid_; e < ca * 2 * cb2; e += NT) {
                 const int a_ = e / (2 * cb2), rest = e - a_ * 2 * cb2;
                 V acc = cmk<V>(0, 0);
+#pragma unroll 1
                 for (int b = 0; b < cb; ++b) acc = cfma(E[(size_t)a_ * cb + b], Aq[(size_t)b * 2 * cb2 + rest], acc);
                 T1[e] = acc;
             }
             bsync<NT>();
             // E'[a'][b'] = sum_{a,s} conj(R[a][s][a']) T1[a][s][b']
+#pragma unroll 1
             for (int e = tid_; e < ca2 * cb2; e += NT) {
                 const int ap = e / cb2, bp = e - ap * cb2;
                 V acc = cmk<V>(0, 0);
+#pragma unroll 1
                 for (int a_ = 0; a_ < ca; ++a_)
+#pragma unroll 1
                     for (int s = 0; s < 2; ++s)
                         acc = cfmac(Rq[((size_t)a_ * 2 + s) * ca2 + ap], T1[((size_t)a_ * 2 + s) * cb2 + bp], acc);
                 E[e] = acc;
@@ -1663,6 +1668,7 @@ struct Engine {
         const int cl = dims[q], cr = dims[q + 1];
         const V* a = base + P.off[q];
         double s = 0;
+#pragma unroll 1
         for (int e = tid_; e < cl * 2 * cr; e += NT) s += (double)a[e].x * a[e].x + (double)a[e].y * a[e].y;
         return block_sum<NT>(s, S.red, tid_);
     }
@@ -1676,6 +1682,7 @@ struct Engine {
         if (P.weight < 0) {
             const uint32_t w = (uint32_t)(shot >> 6), lane = (uint32_t)(shot & 63);
             const uint32_t ng = (P.nchan + 3) / 4;
+#pragma unroll 1
             for (uint32_t g = tid_; g < ng; g += NT) {
                 const U4 u = philox(g, w, 0, TAG_WORD, P.k0, P.k1);
 #pragma unroll
@@ -1695,6 +1702,7 @@ struct Engine {
             bsync<NT>();
             if (tid_ == 0) {  // insertion sort by channel
                 const int cnt = min(nf, MAXF);
+#pragma unroll 1
                 for (int i = 1; i < cnt; ++i) {
                     const uint32_t c = S.fch[i];
                     const uint8_t d = S.fcode[i];
@@ -1708,9 +1716,11 @@ struct Engine {
             uint32_t draw = 0;
             const uint32_t M = P.nchan, W = (uint32_t)P.weight;
             int cnt = 0;
+#pragma unroll 1
             for (uint32_t j = M - W; j < M; ++j) {
                 const uint32_t t = exact_bounded(shot, draw, j + 1, P.k0, P.k1);
                 bool present = false;
+#pragma unroll 1
                 for (int k = 0; k < cnt; ++k) present |= (S.fch[k] == t);
                 const uint32_t v = present ? j : t;
                 if (cnt < MAXF) {
@@ -1720,6 +1730,7 @@ struct Engine {
                 }
                 ++cnt;
             }
+#pragma unroll 1
             for (int k = 0; k < min(cnt, MAXF); ++k) S.fcode[k] = (uint8_t)exact_code(P.chan_kind[S.fch[k]], S.fch[k], shot, P.k0, P.k1);
             nf = cnt;
         }
@@ -1735,7 +1746,9 @@ struct Engine {
         status = 0; disc = 0; degen = 0; chi_peak = 1; nupd = 0; abort_op = -1; flops = 0; sweeps = 0;
         gmem_updates = 0;
         resplits = 0;
+#pragma unroll 1
         for (int q = tid_; q <= P.nq; q += NT) S.dims[q] = 1;
+#pragma unroll 1
         for (int q = tid_; q < P.nq; q += NT) {
             V* a = site(q);
             a[0] = cmk<V>(1, 0);
@@ -1743,16 +1756,20 @@ struct Engine {
             reset_pend(q);
         }
         if (P.phase_cycles && tid_ == 0)
+#pragma unroll 1
             for (int k = 0; k < 8; ++k) S.phase[k] = 0;
         bsync<NT>();
         tick();
         const int nf = faults(shot);
         tock(PH_FAULTS);
         if (nf > MAXF) status = QC_ECAPACITY;
+#pragma unroll 1
         for (uint32_t base = 0; base < P.nops && status == 0; base += OPCH) {
             const uint32_t cnt = min((uint32_t)OPCH, P.nops - base);
+#pragma unroll 1
             for (uint32_t i = tid_; i < cnt; i += NT) S.ops[i] = P.prog[base + i];
             bsync<NT>();
+#pragma unroll 1
             for (uint32_t i = 0; i < cnt && status == 0; ++i) {
                 const MpsOp op = S.ops[i];
                 switch (op.kind) {
@@ -1799,6 +1816,7 @@ struct Engine {
         // finish: apply the gates still pending, then compare with the reference
         tick();
         if (status == 0)
+#pragma unroll 1
             for (int q = 0; q < P.nq; ++q) {
                 bsync<NT>();
                 const V* u = S.pend + q * 4;
@@ -1820,6 +1838,7 @@ struct Engine {
         }
         if (tid_ == 0) {
             if (P.reference) {
+#pragma unroll 1
                 for (int q = 0; q <= P.nq; ++q) P.ref_dims_out[q] = S.dims[q];
                 *P.ref_disc_out = disc;
                 *P.ref_chi_out = chi_peak;
@@ -1855,6 +1874,7 @@ struct Engine {
         }
         tock(PH_FINISH);
         if (P.phase_cycles && tid_ == 0 && !P.reference)
+#pragma unroll 1
             for (int k = 0; k < 8; ++k) atomicAdd(&P.phase_cycles[k], S.phase[k]);
         bsync<NT>();
     }
@@ -2351,9 +2371,6 @@ static qc_status run_engine(CircuitImpl& c, qc_noise noise, const uint64_t* shot
     P.precision = prm.precision;
     P.wmax = wmax;
     P.sweep_cap = sizeof(R) == 4 ? 40 : 60;  // the noiseless reference run always keeps the default
-    // norm tracking (alpha, beta updated by the rotation instead of summed) measured no faster on the
-    // benchmark workload, and its rounding moves near-degenerate cuts: off unless asked for
-    P.track_norms = getenv("QCMPS_NORM_TRACKING") ? 1 : 0;
     {
         int center = 0;
         for (const MpsOp& o : c.mps) {
