@@ -1089,69 +1089,39 @@ struct Engine {
         bsync<NT>();
         V* As = site(q);
         V* Bs = site(q + 1);
-        if (xt && right) {
-            // X = theta' = U S V^H:  A[q] = U (cl, 2, r);  A[q+1] = scale * U^H theta' (r, 2, cr)
+        // The factors, in one pair of loops for the four cases (orthogonalised side xt = theta' or its
+        // conjugate transpose; centre to the right or the left):
+        //   xt,  right: A[q] = U (cl, 2, r);             A[q+1] = scale * U^H theta' (r, 2, cr)
+        //   xt,  left:  A[q] = scale * U S (cl, 2, r);   A[q+1] = V^H = S^-1 U^H theta' (r, 2, cr)
+        //   !xt, left:  A[q+1] = U'^H (r, 2, cr);         A[q] = scale * theta' U' (cl, 2, r)
+        //   !xt, right: A[q+1] = scale * S U'^H (r, 2, cr); A[q] = V' = theta' U' S^-1 (cl, 2, r)
+        // (U, U' = the normalised kept columns of X; theta' = V' S U'^H in the !xt cases.)
+        {
+            const bool plain = xt == right;         // the orthonormal factor unscaled, the projection x scale
+            V* Fo = xt ? As : Bs;                   // orthonormal factor: U (m x r) or U'^H (r x n)
+            V* Fp = xt ? Bs : As;                   // projection: U^H theta' (r x n) or theta' U' (m x r)
+            const int no = xt ? m * r : r * n, dio = xt ? r : n;
 #pragma unroll 1
-            for (int e = tid_; e < m * r; e += NT) {
-                const int i = e / r, k = e - i * r;
+            for (int e = tid_; e < no; e += NT) {
+                const int a = e / dio, b = e - a * dio;
+                const int k = xt ? b : a, i = xt ? a : b;  // kept index, row of X
+                const RS f = plain ? (RS)1 : scale * sig2[perm[k]];
                 const VS u = X[(size_t)perm[k] * ld + i];
-                As[e] = cmk<V>(u.x, u.y);
+                Fo[e] = cmk<V>(u.x * f, (xt ? u.y : -u.y) * f);
             }
+            const int np = xt ? r * n : m * r, dip = xt ? n : r;
 #pragma unroll 1
-            for (int e = tid_; e < r * n; e += NT) {
-                const int k = e / n, j = e - k * n;
-                const VS acc = dot_conj(X + (size_t)perm[k] * ld, T + j, (size_t)n, m);
-                Bs[e] = cmk<V>(acc.x * scale, acc.y * scale);
-            }
-        } else if (!xt && !right) {
-            // X = theta'^H = U' S V'^H:  A[q+1] = U'^H (r, 2, cr);  A[q] = scale * theta' U' (cl, 2, r)
-#pragma unroll 1
-            for (int e = tid_; e < r * n; e += NT) {
-                const int k = e / n, j = e - k * n;
-                const VS u = X[(size_t)perm[k] * ld + j];
-                Bs[e] = cmk<V>(u.x, -u.y);
-            }
-#pragma unroll 1
-            for (int e = tid_; e < m * r; e += NT) {
-                const int i = e / r, k = e - i * r;
-                const VS acc = dot_plain(T + (size_t)i * n, X + (size_t)perm[k] * ld, n);
-                As[e] = cmk<V>(acc.x * scale, acc.y * scale);
-            }
-        } else if (xt) {
-            // X = theta' = U S V^H, centre to the left:  A[q] = scale * U S (cl, 2, r);
-            // A[q+1] = V^H = S^-1 U^H theta' (r, 2, cr)
-#pragma unroll 1
-            for (int e = tid_; e < m * r; e += NT) {
-                const int i = e / r, k = e - i * r;
-                const RS f = scale * sig2[perm[k]];
-                const VS u = X[(size_t)perm[k] * ld + i];
-                As[e] = cmk<V>(u.x * f, u.y * f);
-            }
-#pragma unroll 1
-            for (int e = tid_; e < r * n; e += NT) {
-                const int k = e / n, j = e - k * n;
-                const VS acc = dot_conj(X + (size_t)perm[k] * ld, T + j, (size_t)n, m);
-                const RS svk = sig2[perm[k]];
-                const RS inv = svk > (RS)0 ? fdiv((RS)1, svk) : (RS)0;
-                Bs[e] = cmk<V>(acc.x * inv, acc.y * inv);
-            }
-        } else {
-            // X = theta'^H = U' S V'^H (theta' = V' S U'^H), centre to the right:
-            // A[q] = V' = theta' U' S^-1 (cl, 2, r);  A[q+1] = scale * S U'^H (r, 2, cr)
-#pragma unroll 1
-            for (int e = tid_; e < r * n; e += NT) {
-                const int k = e / n, j = e - k * n;
-                const RS f = scale * sig2[perm[k]];
-                const VS u = X[(size_t)perm[k] * ld + j];
-                Bs[e] = cmk<V>(u.x * f, -u.y * f);
-            }
-#pragma unroll 1
-            for (int e = tid_; e < m * r; e += NT) {
-                const int i = e / r, k = e - i * r;
-                const VS acc = dot_plain(T + (size_t)i * n, X + (size_t)perm[k] * ld, n);
-                const RS svk = sig2[perm[k]];
-                const RS inv = svk > (RS)0 ? fdiv((RS)1, svk) : (RS)0;
-                As[e] = cmk<V>(acc.x * inv, acc.y * inv);
+            for (int e = tid_; e < np; e += NT) {
+                const int a = e / dip, b = e - a * dip;
+                const int k = xt ? a : b, j = xt ? b : a;  // kept index, other index of theta'
+                const VS acc = xt ? dot_conj(X + (size_t)perm[k] * ld, T + j, (size_t)n, m)
+                                  : dot_plain(T + (size_t)j * n, X + (size_t)perm[k] * ld, n);
+                RS f = scale;
+                if (!plain) {
+                    const RS svk = sig2[perm[k]];
+                    f = svk > (RS)0 ? fdiv((RS)1, svk) : (RS)0;
+                }
+                Fp[e] = cmk<V>(acc.x * f, acc.y * f);
             }
         }
         bsync<NT>();
