@@ -115,11 +115,12 @@ def measured_peaks():
 
 
 # DRAM bytes (read + write) per site operation (two-site update or centre move) of the engine, from one
-# ncu capture of the small case (`--case engine-prefix6`: the benchmark circuit's first 6 layers, 1,332
-# survivors, one launch, DRAM counters in one pass; summary under profiles/).  The benchmark launch is too
-# large to capture with counters, so its traffic is this figure times its site operations; valid only
-# for the engine source the capture was taken on (null otherwise).
-ENGINE_TRAFFIC = {"mps_cu_sha256": None, "bytes_per_site_op": None}
+# ncu capture of the small case (`--case engine-60l`: the benchmark's circuit on 1,332 survivors, every
+# warp slot of one launch busy, DRAM counters in one pass; summary under profiles/).  The benchmark launch
+# (8,192 survivors) is larger than the capture rule allows, so its traffic is this figure times its site
+# operations; valid only for the engine source the capture was taken on (null otherwise).
+ENGINE_TRAFFIC = {"mps_cu_sha256": "71905de9d1c3db5e04ad6399fc12e35362ed912ff432a6a63a5f39d0a3604465",
+                  "bytes_per_site_op": 663.70}  # 5.476e9 read + 16.860e9 written / 33,653,719 site operations
 
 
 def engine_traffic(site_ops):
@@ -676,15 +677,16 @@ def main():
     achieved = flops_timed / (eng_ms / 1e3) / 1e12 if eng_ms > 0 else 0.0
 
     # end-to-end leg through the C ABI with host buffers: the survivor list goes to the host and
-    # back (pinned), per-shot results and counts come back to the host
-    e2e_steps = max(1, min(args.steps, 2))
+    # back (pinned), per-shot results and counts come back to the host; the same shot ranges as the
+    # first timed steps, so that the two numbers measure the same work
+    e2e_steps = max(1, args.steps)
     pin_surv = torch.empty(drawn, dtype=torch.int64, pin_memory=True)
     pin_res = torch.empty(drawn * q.SHOT_DTYPE.itemsize, dtype=torch.uint8, pin_memory=True)
     torch.cuda.synchronize()
     w0 = time.perf_counter()
     e2e_acc, h2d, d2h = 0, 0, 0
     for k in range(e2e_steps):
-        out = q.pauli_prescreen(circ, shot0_of(10_000 + k), drawn, p=args.p, seed=args.seed, kept_mask=mask_buf,
+        out = q.pauli_prescreen(circ, shot0_of(args.warmup + k), drawn, p=args.p, seed=args.seed, kept_mask=mask_buf,
                                 survivors=surv_buf)
         n = int(out["survivors"].numel())
         pin_surv[:n].copy_(out["survivors"], non_blocking=False)
@@ -748,8 +750,8 @@ def main():
         "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                      "frac": achieved / alu_peak if alu_peak else None, "traffic": (engine_traffic(int(site_ops_dev)) / len(kernel_ms) if engine_traffic(1) else None),
                      "traffic_note": "DRAM read+write bytes per engine launch: bytes per site operation from an "
-                                     "ncu capture of the 6-layer prefix case x this launch's site operations "
-                                     "(null when the engine source changed since the capture)",
+                                     "ncu capture of this workload on 1,332 survivors (--case engine-60l) x this "
+                                     "launch's site operations (null when the engine source changed since)",
                      "kernel": ("engine_kernel<float,%d> (%s, %d KB work area, autotuned)" % (
                          launch.get("threads", 0), "one warp per shot" if launch.get("threads") == 32
                          else "one CTA per shot", launch.get("kb", 0))),
