@@ -49,16 +49,17 @@ __device__ __forceinline__ V dot_conj(const V* u, const V* t, size_t ts, int n) 
     if constexpr (sizeof(V) == 8) {
         float2 a0 = make_float2(0.f, 0.f), a1 = a0, b0 = a0, b1 = a0;
         int i = 0;
+        const V* tp = t;  // t[i * ts] walked by pointer
 #pragma unroll 1
-        for (; i + 1 < n; i += 2) {
-            const float2 x0 = u[i], y0 = t[(size_t)i * ts], x1 = u[i + 1], y1 = t[(size_t)(i + 1) * ts];
+        for (; i + 1 < n; i += 2, tp += 2 * ts) {
+            const float2 x0 = u[i], y0 = tp[0], x1 = u[i + 1], y1 = tp[ts];
             a0 = __ffma2_rn(make_float2(x0.x, x0.x), y0, a0);                      // (ux tx, ux ty)
             b0 = __ffma2_rn(make_float2(x0.y, -x0.y), make_float2(y0.y, y0.x), b0);  // (uy ty, -uy tx)
             a1 = __ffma2_rn(make_float2(x1.x, x1.x), y1, a1);
             b1 = __ffma2_rn(make_float2(x1.y, -x1.y), make_float2(y1.y, y1.x), b1);
         }
         if (i < n) {
-            const float2 x0 = u[i], y0 = t[(size_t)i * ts];
+            const float2 x0 = u[i], y0 = tp[0];
             a0 = __ffma2_rn(make_float2(x0.x, x0.x), y0, a0);
             b0 = __ffma2_rn(make_float2(x0.y, -x0.y), make_float2(y0.y, y0.x), b0);
         }
@@ -360,9 +361,12 @@ struct Engine {
         using VS = typename VecOf<RS>::T;
         if constexpr (sizeof(RS) == 4) {
             float2 sa = make_float2(0.f, 0.f), sb = sa, sg = sa, sh = sa;
+            const float2* pa = a + gl;
+            const float2* pb = b + gl;
+            const float2* const pe = a + rows;
 #pragma unroll 1
-            for (int i = gl; i < rows; i += g) {
-                const float2 x = a[i], y = b[i];
+            for (; pa < pe; pa += g, pb += g) {  // rows gl, gl + g, ... walked by pointer
+                const float2 x = *pa, y = *pb;
                 sa = __ffma2_rn(x, x, sa);
                 sb = __ffma2_rn(y, y, sb);
                 sg = __ffma2_rn(x, y, sg);                            // (x.re y.re, x.im y.im)
@@ -393,16 +397,19 @@ struct Engine {
         if constexpr (sizeof(RS) == 4) {
             const float2 cc = make_float2(c, c), nw = make_float2(-wr, -wr), ws = make_float2(wi, -wi);
             const float2 wp = make_float2(wr, wr);
+            float2* pa = a + gl;
+            float2* pb = b + gl;
+            float2* const pe = a + rows;
 #pragma unroll 1
-            for (int i = gl; i < rows; i += g) {
-                const float2 x = a[i], y = b[i];
+            for (; pa < pe; pa += g, pb += g) {
+                const float2 x = *pa, y = *pb;
                 float2 t = __fmul2_rn(nw, y);                          // -w y
                 t = __ffma2_rn(ws, make_float2(y.y, y.x), t);
                 float2 u = __fmul2_rn(cc, y);                          // conj(w) x + c y
                 u = __ffma2_rn(wp, x, u);
                 u = __ffma2_rn(ws, make_float2(x.y, x.x), u);
-                a[i] = __ffma2_rn(cc, x, t);
-                b[i] = u;
+                *pa = __ffma2_rn(cc, x, t);
+                *pb = u;
             }
         } else {
 #pragma unroll 1
@@ -980,10 +987,11 @@ struct Engine {
             const V* a1 = a0 + cm;
             if constexpr (sizeof(RS) == 4) {  // complex MACs as two paired FP32 FMAs each
                 float2 t0 = make_float2(0.f, 0.f), t1 = t0, t2 = t0, t3 = t0;
+                const V* bk = B + r;  // B[k, t', r] walked by pointer (one add per k instead of index products)
 #pragma unroll 1
-                for (int k = 0; k < cm; ++k) {
+                for (int k = 0; k < cm; ++k, bk += n) {
                     const float2 x0 = a0[k], x1 = a1[k];
-                    const float2 y0 = B[(size_t)k * n + r], y1 = B[(size_t)k * n + cr + r];
+                    const float2 y0 = bk[0], y1 = bk[cr];
                     const float2 x0r = make_float2(x0.x, x0.x), x0i = make_float2(-x0.y, x0.y);
                     const float2 x1r = make_float2(x1.x, x1.x), x1i = make_float2(-x1.y, x1.y);
                     const float2 y0s = make_float2(y0.y, y0.x), y1s = make_float2(y1.y, y1.x);
@@ -1143,9 +1151,9 @@ struct Engine {
     // Each column is orthogonalised against the kept ones, the pass repeated while it removes more
     // than half of the column's squared norm (the Daniel-Gragg-Kaufman-Stewart test), so every kept
     // column is orthogonal to the earlier ones to rounding.  A column whose remainder falls to the
-    // floor depends on the kept ones and is dropped.  On return the kept columns of X are
-    // orthonormal, perm[0..k) lists them in order, and Rm (row-major, k x cols, zeroed by the
-    // caller) holds R: X_in = Q R.  hb: scratch of cols elements.  Returns k.
+    // floor depends on the kept ones and is dropped.  On return columns 0..k-1 of X hold the
+    // orthonormal kept columns in order (the i-th came from column perm[i]), and Rm (row-major,
+    // k x cols, zeroed by the caller) holds R: X_in = Q R.  hb: scratch of cols elements.  Returns k.
     __device__ int gram_schmidt(V* X, int rows, int cols, int ld, V* Rm, V* hb, int* perm, R floor2,
                                 double& dropped) {
         int k = 0;
@@ -1167,7 +1175,7 @@ struct Engine {
                     for (int base = wid * G; base < k; base += NW * G) {
                         const int i = base + grp;
                         const bool act = i < k;
-                        const V* qi = X + (size_t)perm[act ? i : 0] * ld;
+                        const V* qi = X + (size_t)(act ? i : 0) * ld;
                         R hr = 0, hi = 0;
                         if (act) {
                             if constexpr (sizeof(R) == 4) {  // paired FP32 FMAs, as in the Jacobi
@@ -1205,14 +1213,16 @@ struct Engine {
                 for (int t = tid_; t < rows; t += NT) {  // x -= sum_i h_i q_i (two partial sums)
                     V acc = x[t], acc1 = cmk<V>(0, 0);
                     int i = 0;
-                    for (; i + 1 < k; i += 2) {
-                        const V h = hb[i], u = X[(size_t)perm[i] * ld + t];
-                        const V h1 = hb[i + 1], u1 = X[(size_t)perm[i + 1] * ld + t];
+                    const V* qt = X + t;  // row t of the kept columns 0, 1, ... (stored in order)
+#pragma unroll 1
+                    for (; i + 1 < k; i += 2, qt += 2 * ld) {
+                        const V h = hb[i], u = qt[0];
+                        const V h1 = hb[i + 1], u1 = qt[ld];
                         acc = cmk<V>(acc.x - (h.x * u.x - h.y * u.y), acc.y - (h.x * u.y + h.y * u.x));
                         acc1 = cmk<V>(acc1.x + (h1.x * u1.x - h1.y * u1.y), acc1.y + (h1.x * u1.y + h1.y * u1.x));
                     }
                     if (i < k) {
-                        const V h = hb[i], u = X[(size_t)perm[i] * ld + t];
+                        const V h = hb[i], u = qt[0];
                         acc = cmk<V>(acc.x - (h.x * u.x - h.y * u.y), acc.y - (h.x * u.y + h.y * u.x));
                     }
                     acc = cmk<V>(acc.x - acc1.x, acc.y - acc1.y);
@@ -1226,9 +1236,12 @@ struct Engine {
                 if (done) break;
             }
             if (nnow > floor2) {
+                // the k-th kept column is stored normalised in column k (k <= j; columns k .. j-1 hold
+                // nothing that is still needed), so the kept columns stay contiguous
                 const R nr = sqrt(nnow), inv = (R)1 / nr;
+                V* xk = X + (size_t)k * ld;
 #pragma unroll 1
-                for (int t = tid_; t < rows; t += NT) x[t] = cmk<V>(x[t].x * inv, x[t].y * inv);
+                for (int t = tid_; t < rows; t += NT) xk[t] = cmk<V>(x[t].x * inv, x[t].y * inv);
                 if (tid_ == 0) {
                     Rm[(size_t)k * cols + j] = cmk<V>(nr, (R)0);
                     perm[k] = j;
@@ -1320,7 +1333,7 @@ struct Engine {
 #pragma unroll 1
             for (int e = tid_; e < m * r; e += NT) {
                 const int i = e / r, kk = e - i * r;
-                A[e] = X[(size_t)perm[kk] * ld + i];
+                A[e] = X[(size_t)kk * ld + i];
             }
 #pragma unroll 1
             for (int e = tid_; e < r * n; e += NT) B[e] = tcopy[e];
@@ -1339,7 +1352,7 @@ struct Engine {
 #pragma unroll 1
             for (int e = tid_; e < r * n; e += NT) {
                 const int kk = e / n, jn = e - kk * n;
-                const V u = X[(size_t)perm[kk] * ld + jn];
+                const V u = X[(size_t)kk * ld + jn];
                 B[e] = cmk<V>(u.x, -u.y);
             }
 #pragma unroll 1
@@ -1477,7 +1490,7 @@ struct Engine {
                     const int kk = e / n, rem = e - kk * n;
                     V v = cmk<V>(0, 0);
                     if (rem < cr) {
-                        const V u = X[(size_t)perm[kk] * ld + rem];
+                        const V u = X[(size_t)kk * ld + rem];
                         v = cmk<V>(u.x, -u.y);
                     }
                     B[e] = v;
@@ -1487,7 +1500,7 @@ struct Engine {
 #pragma unroll 1
                 for (int e = tid_; e < cl * 2 * k; e += NT) {
                     const int l = e / (2 * k), rem = e - l * 2 * k;
-                    A[e] = rem < k ? X[(size_t)perm[rem] * ld + l] : cmk<V>(0, 0);
+                    A[e] = rem < k ? X[(size_t)rem * ld + l] : cmk<V>(0, 0);
                 }
 #pragma unroll 1
                 for (int e = tid_; e < k * cols; e += NT) B[e] = Rm[e];
