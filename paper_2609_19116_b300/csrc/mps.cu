@@ -684,13 +684,13 @@ struct Engine {
             int r = 1 + __reduce_add_sync(full, cnt);
             r = min(r, P.chi_trunc);
             r = min(r, max(nz, 1));
-            double kl = 0, tl = 0;
+            // dropped = the tail sum from position r: the lane whose chunk holds r adds its chunk's part
+            // to the sum of the later chunks; kept = total - dropped
+            double tr = after;
 #pragma unroll 1
-            for (int k = k0; k < k1; ++k) {
-                const double v = (double)sig2[perm[k]];
-                if (k < r) kl += v; else tl += v;
-            }
-            const double kept = warp_sum<double>(kl), dropped = warp_sum<double>(tl);
+            for (int k = k1 - 1; k >= k0 && k >= r; --k) tr += (double)sig2[perm[k]];
+            const double dropped = r < cols ? __shfl_sync(full, tr, min(31, r / c)) : 0.0;
+            const double kept = tot - dropped;
             if (lane == 0) {
                 int dg = 0;
                 // a cut inside a cluster: the last kept and the first dropped value agree to what the
@@ -1180,9 +1180,12 @@ struct Engine {
                         if (act) {
                             if constexpr (sizeof(R) == 4) {  // paired FP32 FMAs, as in the Jacobi
                                 float2 s1 = make_float2(0.f, 0.f), s2 = s1;
+                                const float2* pq = qi + gl;
+                                const float2* px = x + gl;
+                                const float2* const pe = qi + rows;
 #pragma unroll 1
-                                for (int t = gl; t < rows; t += g) {
-                                    const float2 u0 = qi[t], x0 = x[t];
+                                for (; pq < pe; pq += g, px += g) {
+                                    const float2 u0 = *pq, x0 = *px;
                                     s1 = __ffma2_rn(u0, x0, s1);                          // (q.re x.re, q.im x.im)
                                     s2 = __ffma2_rn(u0, make_float2(x0.y, x0.x), s2);     // (q.re x.im, q.im x.re)
                                 }
