@@ -21,7 +21,6 @@ import os
 import statistics
 import subprocess
 import sys
-import threading
 import time
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -59,27 +58,41 @@ def parse_args():
 
 # ---- clocks during the timed region ----------------------------------------------------------
 class ClockSampler:
+    """nvidia-smi sampling the SM clock and throttle reasons every 200 ms into a temporary file, read
+    after the timed region (a Python thread reading a pipe instead slowed the timed steps by ~20 %:
+    the host's CUDA calls between engine launches waited on it)."""
+
     def __init__(self, index=0):
         self.index = index
         self.proc = None
-        self.lines = []
+        self.path = None
 
     def start(self):
+        import tempfile
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
+            fd, self.path = tempfile.mkstemp(prefix="qc_clocks_", suffix=".csv")
+            self.out = os.fdopen(fd, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
                                           "-lms", "200", "-i", str(self.index)],
-                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-            self.thread = threading.Thread(target=self._read, daemon=True)
-            self.thread.start()
+                                         stdout=self.out, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
 
-    def _read(self):
-        for line in self.proc.stdout:
-            self.lines.append(line.strip())
+    def _lines(self):
+        try:
+            with open(self.path) as f:
+                return [ln.strip() for ln in f if ln.strip()]
+        except (OSError, TypeError):
+            return []
+
+    def wait_first(self, timeout=10.0):
+        """Blocks until the first sample arrived: nvidia-smi's start-up falls before the timed region."""
+        t0 = time.perf_counter()
+        while self.proc is not None and not self._lines() and time.perf_counter() - t0 < timeout:
+            time.sleep(0.05)
 
     def stop(self):
         if self.proc is None:
@@ -89,9 +102,15 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
+        self.out.close()
+        lines = self._lines()
+        try:
+            os.unlink(self.path)
+        except OSError:
+            pass
         sm, smax, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ln in lines:
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
                 continue
@@ -119,8 +138,8 @@ def measured_peaks():
 # warp slot of one launch busy, DRAM counters in one pass; summary under profiles/).  The benchmark launch
 # (8,192 survivors) is larger than the capture rule allows, so its traffic is this figure times its site
 # operations; valid only for the engine source the capture was taken on (null otherwise).
-ENGINE_TRAFFIC = {"mps_cu_sha256": "71905de9d1c3db5e04ad6399fc12e35362ed912ff432a6a63a5f39d0a3604465",
-                  "bytes_per_site_op": 663.70}  # 5.476e9 read + 16.860e9 written / 33,653,719 site operations
+ENGINE_TRAFFIC = {"mps_cu_sha256": "a5e02f7cdc08f3a094b9e92cd0daf5de2014f13bd4884b467459c89d51d154e8",
+                  "bytes_per_site_op": 668.88}  # 5.520e9 read + 16.990e9 written / 33,653,719 site operations
 
 
 def engine_traffic(site_ops):
@@ -620,15 +639,19 @@ def main():
                                        cutoff=args.cutoff, precision=q.QC_C64, per_shot=True,
                                        per_shot_buf=shot_buf, copy_back=False, launch=launch)
         e1.record(stream)
+        # algorithmic flops and site operations of this step's shots, summed on the device from the
+        # records (in the warm-up steps too, so that the reduction kernels are loaded before the timed
+        # region: their first, lazy load took ~1 s)
+        recs = shot_buf[: surv.numel() * q.SHOT_DTYPE.itemsize].view(torch.float64)
+        recs = recs.view(-1, q.SHOT_DTYPE.itemsize // 8)
+        f_step = recs[:, q.SHOT_DTYPE.fields["alg_flops"][1] // 8].sum()
+        ops_i32 = shot_buf[: surv.numel() * q.SHOT_DTYPE.itemsize].view(torch.int32).view(
+            -1, q.SHOT_DTYPE.itemsize // 4)
+        o_step = ops_i32[:, q.SHOT_DTYPE.fields["n_updates"][1] // 4].sum()
+        flops_dev.add_(f_step)  # (the warm-up's sums are cleared before the timed region)
+        site_ops_dev.add_(o_step)
         if timed:
             kernel_ms.append((e0, e1, int(surv.numel())))
-            # algorithmic flops of this step's shots, summed on the device (alg_flops of each record)
-            recs = shot_buf[: surv.numel() * q.SHOT_DTYPE.itemsize].view(torch.float64)
-            recs = recs.view(-1, q.SHOT_DTYPE.itemsize // 8)
-            flops_dev.add_(recs[:, q.SHOT_DTYPE.fields["alg_flops"][1] // 8].sum())
-            ops_i32 = shot_buf[: surv.numel() * q.SHOT_DTYPE.itemsize].view(torch.int32).view(
-                -1, q.SHOT_DTYPE.itemsize // 4)
-            site_ops_dev.add_(ops_i32[:, q.SHOT_DTYPE.fields["n_updates"][1] // 4].sum())
         last["counts"] = counts
         last["n"] = int(surv.numel())
         return int(counts[:, 1].sum()), int(surv.numel())
@@ -636,11 +659,14 @@ def main():
     # warm-up (also builds the cached reference state)
     for k in range(args.warmup):
         step(k, False)
+    flops_dev.zero_()
+    site_ops_dev.zero_()
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     clk = ClockSampler(local)
     clk.start()
+    clk.wait_first()
     t_start = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()

@@ -703,12 +703,12 @@ struct Engine {
                 // FP32 noise level drops at most cutoff x total whichever of them it keeps
                 if (r < cols) {
                     const double a2 = (double)sig2[perm[r - 1]], b2 = (double)sig2[perm[r]];
-                    const double rel = sizeof(RS) == 8 ? 2e-8 + 1e-16 : 32.0 * FLT_EPSILON * sqrt((double)rows);
+                    const double rel = sizeof(RS) == 8 ? 2e-8 + 1e-16 : 32.0 * FLT_EPSILON * (double)sqrtf((float)rows);
                     const double sig = sizeof(RS) == 8 ? (double)floor2 : fmax((double)floor2, P.cutoff * tot);
                     dg = b2 > sig && a2 <= b2 * (1.0 + rel);
                 }
                 S.red[40] = tot > 0 ? dropped / tot : 0.0;
-                S.red[41] = kept > 0 ? 1.0 / sqrt(kept) : 0.0;
+                S.red[41] = kept > 0 ? rsqrt(kept) : 0.0;  // applied in the working precision
                 S.red[42] = (double)r;
                 S.red[43] = (double)dg;
             }
