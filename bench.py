@@ -59,8 +59,7 @@ def parse_args():
 # ---- clocks during the timed region ----------------------------------------------------------
 class ClockSampler:
     """nvidia-smi sampling the SM clock and throttle reasons every 200 ms into a temporary file, read
-    after the timed region (a Python thread reading a pipe instead slowed the timed steps by ~20 %:
-    the host's CUDA calls between engine launches waited on it)."""
+    after the timed region."""
 
     def __init__(self, index=0):
         self.index = index
