@@ -137,8 +137,8 @@ def measured_peaks():
 # warp slot of one launch busy, DRAM counters in one pass; summary under profiles/).  The benchmark launch
 # (8,192 survivors) is larger than the capture rule allows, so its traffic is this figure times its site
 # operations; valid only for the engine source the capture was taken on (null otherwise).
-ENGINE_TRAFFIC = {"mps_cu_sha256": "a5e02f7cdc08f3a094b9e92cd0daf5de2014f13bd4884b467459c89d51d154e8",
-                  "bytes_per_site_op": 668.88}  # 5.520e9 read + 16.990e9 written / 33,653,719 site operations
+ENGINE_TRAFFIC = {"mps_cu_sha256": "43b2b2b9dc50246062769e8c157112836e2ff7cc71088b40c7c32336d2b868b9",
+                  "bytes_per_site_op": 669.24}  # 5.523e9 read + 16.999e9 written / 33,653,719 site operations
 
 
 def engine_traffic(site_ops):

@@ -2466,7 +2466,11 @@ static qc_status run_engine(CircuitImpl& c, qc_noise noise, const uint64_t* shot
         const bool small = first && ref->chi_peak <= 64;
         // the re-run pass (few shots, large theta) takes the largest CTA whether or not the GPU is shared
         LaunchCfg cf = first ? rule_cfg(small, n, nsm, shared_gpu, NT_BIG) : LaunchCfg{NT_BIG, 200, 1, 0};
-        if (env_cfg(cf, NT_BIG)) return cf;
+        if (env_cfg(cf, NT_BIG)) {
+            // the re-run pass holds the shots a one-warp engine cannot finish: never a warp
+            if (!first && cf.variant == 32) cf = LaunchCfg{NT_BIG, 200, 1, 0};
+            return cf;
+        }
         if (first && !shared_gpu && n >= 2ull * (uint64_t)nsm && !getenv("QCMPS_NO_TUNE"))
             cf = tuned_cfg<R, NT_BIG>(c, Pp, Lp, ref->state, cp, op, *ref, shots_dev, n, s, nsm, dev, small, cf);
         return cf;

@@ -223,6 +223,27 @@ def test_subset_sampling_chi1024_matches_oracle():
         _compare(res, ref, 1e-4, allow_flip=1)
 
 
+def test_warp_engine_defers_fp64_resplits_to_the_cta_rerun(monkeypatch):
+    """The one-warp engine has no FP64 split: a complex64 shot that meets a cut inside a cluster there is
+    set aside and re-run from the start on the 512-thread CTA, which redoes such splits in FP64.  A forced
+    warp launch of 300 noiseless shots of the clustered case (more shots than SMs): every record ends with
+    status 0 and fp64_resplits > 0 (the re-run's record replaced the deferred one), and the counts match
+    those of the CTA launch, which re-splits in place."""
+    q = lib_ready()
+    text = random_circuit(10, 300, seed=3, max_dist=2, noise=False, one_q=("H", "T", "S"), two_q=("CX", "CZ"))
+    c = q.Circuit(text)
+    shots = dev_shots(list(range(300)))
+    monkeypatch.setenv("QCMPS_ENGINE", "warp")
+    cw, rw = q.mps_sample_batch(c, shots, p=0.0, seed=0, chi_max=4, cutoff=0.0, precision=q.QC_C64)
+    monkeypatch.setenv("QCMPS_ENGINE", "cta")
+    cc, rc = q.mps_sample_batch(c, shots, p=0.0, seed=0, chi_max=4, cutoff=0.0, precision=q.QC_C64)
+    assert (rw["status"] == 0).all(), np.unique(rw["status"])
+    assert (rw["fp64_resplits"] > 0).all()
+    assert np.array_equal(rw["shot"], rc["shot"])
+    assert np.array_equal(rw["fp64_resplits"], rc["fp64_resplits"])
+    assert np.array_equal(cw, cc)
+
+
 def test_fp64_resplit_of_cuts_inside_clusters():
     """complex64 with chi_max below the Schmidt rank on Clifford+T circuits, whose spectra have flat
     clusters: a truncation that cuts inside a cluster FP32 cannot resolve is redone in FP64
