@@ -184,7 +184,9 @@ typedef struct {
     int32_t gmem_updates;    /* two-site updates whose Jacobi matrix did not fit the engine's shared
                                 memory and was rotated in global memory (blocked Jacobi) */
     int32_t fp64_resplits;   /* QC_C64: splits redone in FP64 because the truncation cut inside a cluster
-                                of singular values that FP32 cannot tell apart */
+                                of singular values that FP32 cannot tell apart and dropped more than the
+                                cutoff's weight (a shot that meets one in a one-warp engine is re-run
+                                from the start by a 512-thread engine, which counts them here) */
 } qc_shot_result;
 
 /* Simulate the given shots (typically pre-screen survivors) as MPS: single-site gates in place;
@@ -198,8 +200,13 @@ typedef struct {
  *   per_w          host array of w_max+1 counts, ACCUMULATED into (bin w_max collects w >= w_max):
  *                  n = simulated shots, n_acc = accepted, n_err = accepted with a logical error
  *   per_shot_dev   optional device array of nshots results
- * Synchronises `stream` before returning.  QC_EINVAL if the noiseless circuit has a measurement
- * that is not deterministically 0.  Per-shot failures are reported in per_shot_dev status. */
+ * Engines: one warp per shot for circuits whose noiseless run stays at bond 64, else one CTA per
+ * shot, in slots of a capacity bucket; shots that outgrow the bucket (or need an FP64 re-split in a
+ * one-warp engine) are re-run at full capacity in a second launch, their records replaced.
+ * Synchronises `stream` before returning.  QC_EINVAL for chi_max outside [1, 1024], a negative
+ * cutoff, an unknown precision, or a noiseless circuit with a measurement that is not
+ * deterministically 0 (the argument checks come before any device work).  Per-shot failures are
+ * reported in per_shot_dev status. */
 qc_status mps_sample_batch(const qc_circuit* circuit, qc_noise noise, const uint64_t* shots_dev,
                            uint64_t nshots, qc_mps_params params, qc_counts* per_w,
                            int32_t w_max, qc_shot_result* per_shot_dev, void* stream);
