@@ -518,9 +518,10 @@ def c2_leg(q, args, peaks):
                                      "word; lane walks of faulted words not counted"}}
 
 
-def chi_rows_leg(q, circ, args, chis=(64, 128), survivors=2048):
-    """Config 3 at the other chi_max values: one device-timed batch of `survivors` pre-screen survivors
-    of the 49-qubit workload per chi_max (complex64, cutoff 1e-10)."""
+def chi_rows_leg(q, circ, args, chis=(64, 128)):
+    """Config 3 at the other chi_max values: one device-timed batch of 8,192 pre-screen survivors (the
+    config's launch size) of the 49-qubit workload per chi_max (complex64, cutoff 1e-10)."""
+    survivors = args.survivors
     out = {}
     pre = q.pauli_prescreen(circ, 64 * 50_000_000, int(math.ceil(survivors / 0.00125 / 64.0)) * 64 * 2,
                             p=args.p, seed=args.seed)
